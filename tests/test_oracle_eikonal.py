@@ -1,0 +1,177 @@
+"""Pins of the oracle's eikonal solve (Eq. hopflax_global / hopflax_local,
+Algorithm 2) against what the mathematics fixes independently of it:
+planar fronts reproduced exactly by P1 elements, the closed-form point
+source with a constant metric (lower bound + mesh convergence), an
+edge-graph Dijkstra upper bound built with scipy, and order independence of
+the monotone fixed-point iteration (worklist vs. the literal Jacobi sweeps of
+Algorithm 2)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.csgraph as cg
+
+from oracle import oracle as O
+from paper_2308_08410_gb300 import synth as S
+
+
+def conduction_tensor(cf, ct, f):
+    f = np.asarray(f, float)
+    f = f / np.linalg.norm(f)
+    return ct ** 2 * np.eye(3) + (cf ** 2 - ct ** 2) * np.outer(f, f)
+
+
+def uniform_params(mesh, cf=0.6, ct=0.3, f=(1.0, 0.3, 0.2)):
+    fib = np.tile(np.asarray(f, np.float32) / np.linalg.norm(f), (mesh.n_t, 1)).astype(np.float32)
+    return fib, np.full(mesh.n_t, cf, np.float32), np.full(mesh.n_t, ct, np.float32)
+
+
+def test_planar_front_exact():
+    """phi = c + g.x with g^T M g = 1 solves Eq. (1) exactly and is P1; fixing
+    it on the boundary, every interior vertex reproduces it (Cauchy-Schwarz
+    gives >=, the backward characteristic hits a face of the vertex star)."""
+    n, side = 8, 1.0
+    mesh = S.kuhn_cube(n, side)
+    fib, cf, ct = uniform_params(mesh)
+    M = conduction_tensor(float(cf[0]), float(ct[0]), fib[0].astype(float))
+    for u in ([1, 0, 0], [0.3, -0.8, 0.5], [-0.2, 0.1, -1.0]):
+        u = np.asarray(u, float) / np.linalg.norm(u)
+        g = u / np.sqrt(u @ M @ u)
+        x = mesh.xyz.astype(float)
+        exact = 10.0 + x @ g
+        bnd = np.nonzero(np.any((x <= 1e-9) | (x >= side - 1e-9), axis=1))[0]
+        ons = S.Onsets(S.ONSET_NODAL, bnd.astype(np.int32), exact[bnd].astype(np.float32))
+        ek = O.eikonal(mesh, fib, cf, ct, ons)
+        inner = np.setdiff1d(np.arange(mesh.n_v), bnd)
+        # onsets are float32; compare with the same rounding of the boundary
+        ref = 10.0 + x @ g
+        np.testing.assert_allclose(ek["phi"][inner], ref[inner], rtol=2e-7, atol=0)
+        err = np.abs(ek["phi"][inner] - ref[inner]).max()
+        assert err < 2e-6
+
+
+def test_point_source_lower_bound_and_convergence():
+    """Constant metric, nodal point source at the cube centre: the discrete
+    solution is >= t + ||v - x0||_D (convexity of the distance along faces)
+    and its error decreases under refinement (Sec. II-A, convergence to the
+    viscosity solution)."""
+    errs = []
+    for n in (9, 17, 33):
+        mesh = S.kuhn_cube(n, 1.0)
+        fib, cf, ct = uniform_params(mesh)
+        D = np.linalg.inv(conduction_tensor(float(cf[0]), float(ct[0]), fib[0].astype(float)))
+        c = (n - 1) // 2
+        src = c + n * (c + n * c)
+        ons = S.Onsets(S.ONSET_NODAL, np.array([src], np.int32), np.array([0.0], np.float32))
+        ek = O.eikonal(mesh, fib, cf, ct, ons)
+        w = mesh.xyz.astype(float) - mesh.xyz[src].astype(float)
+        exact = np.sqrt(np.einsum("ni,ij,nj->n", w, D, w))
+        assert np.all(ek["phi"] >= exact - 1e-12)
+        errs.append(np.max(ek["phi"] - exact))
+    assert errs[0] / errs[1] > 1.4 and errs[1] / errs[2] > 1.4, errs
+
+
+def _dijkstra_bound(mesh, fib, cf, ct, ons):
+    """Edge-graph distances with edge weight min_j ||e||_{D_j} over the tets
+    j holding the edge; onsets enter through a virtual source."""
+    x = mesh.xyz.astype(float)
+    pairs = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+    rows, cols, wts = [], [], []
+    Ds = np.linalg.inv(np.stack([conduction_tensor(float(cf[j]), float(ct[j]), fib[j].astype(float))
+                                 for j in range(mesh.n_t)]))
+    for a, b in pairs:
+        va, vb = mesh.tets[:, a], mesh.tets[:, b]
+        e = x[vb] - x[va]
+        w = np.sqrt(np.einsum("ni,nij,nj->n", e, Ds, e))
+        rows += [va, vb]
+        cols += [vb, va]
+        wts += [w, w]
+    rows, cols, wts = map(np.concatenate, (rows, cols, wts))
+    order = np.lexsort((wts, cols, rows))
+    rows, cols, wts = rows[order], cols[order], wts[order]
+    keep = np.ones(len(rows), bool)
+    keep[1:] = (rows[1:] != rows[:-1]) | (cols[1:] != cols[:-1])  # min weight per edge
+    n = mesh.n_v
+    src_r = np.full(ons.K, n)
+    R = np.concatenate([rows[keep], src_r])
+    Cc = np.concatenate([cols[keep], ons.idx])
+    W = np.concatenate([wts[keep], ons.t.astype(float) + 1e-300])
+    G = sp.csr_matrix((W, (R, Cc)), shape=(n + 1, n + 1))
+    return cg.dijkstra(G, directed=True, indices=n)[:n]
+
+
+def test_dijkstra_upper_bound():
+    p = S.make_c1(n=10)
+    ek = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    dj = _dijkstra_bound(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    assert np.all(ek["phi"] <= dj + 1e-12 * np.maximum(1, dj))
+    # and the bound is not trivially loose
+    assert np.mean(ek["phi"] < dj - 1e-9) > 0.3
+
+
+def test_order_independence():
+    """The Hopf-Lax operator with the exact local solver is monotone:
+    Gauss-Seidel (heap / FIFO worklists) and the Jacobi sweeps of Algorithm 2
+    reach the same fixed point."""
+    p = S.make_c1(n=12)
+    res = [O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, order=o)
+           for o in (O.ORDER_HEAP, O.ORDER_FIFO, O.ORDER_JACOBI)]
+    for r in res[1:]:
+        np.testing.assert_allclose(r["phi"], res[0]["phi"], rtol=1e-10)
+    for r in res:
+        assert r["stats"]["max_fixed_point_residual"] < 1e-12
+        assert r["stats"]["unreached"] == 0
+
+
+def test_fista_mode_orders_bracketed():
+    """With Algorithm 1 after n_f steps the face values are only upper bounds
+    and not monotone in Phi, so the result depends on the update order; every
+    order stays between the exact solution and the FISTA error."""
+    p = S.make_c1(n=12)
+    ex = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)["phi"]
+    for o in (O.ORDER_HEAP, O.ORDER_FIFO, O.ORDER_JACOBI):
+        fi = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, mode=O.FISTA, n_f=24, order=o)["phi"]
+        rel = (fi - ex) / np.maximum(1, ex)
+        assert rel.min() > -1e-12 and rel.max() < 1e-2
+
+
+def test_fista_mode_upper_bounds_exact():
+    """Algorithm 1 returns a feasible point, so every face value and hence the
+    FISTA-mode solution is >= the exact one, and close to it for n_f = 64."""
+    p = S.make_c1(n=10)
+    ex = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, mode=O.EXACT)
+    fi = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, mode=O.FISTA, n_f=64)
+    assert np.all(fi["phi"] >= ex["phi"] - 1e-12 * np.maximum(1, ex["phi"]))
+    assert np.max((fi["phi"] - ex["phi"]) / np.maximum(1, ex["phi"])) < 1e-3
+
+
+def test_element_onset_values():
+    """Eq. (upwind_xi): with a constant metric the vertices of the onset tet
+    take t + ||v - x||_D, and everywhere phi >= t + ||v - x||_D."""
+    mesh = S.kuhn_cube(7, 1.0)
+    fib, cf, ct = uniform_params(mesh)
+    D = np.linalg.inv(conduction_tensor(float(cf[0]), float(ct[0]), fib[0].astype(float)))
+    ons = S.onsets_element(mesh, 1, seed=3, tmin=2.0, tmax=3.0)
+    ek = O.eikonal(mesh, fib, cf, ct, ons)
+    tet = mesh.tets[ons.idx[0]]
+    x0 = (ons.bary[0].astype(float)[:, None] * mesh.xyz[tet].astype(float)).sum(0)
+    w = mesh.xyz.astype(float) - x0
+    exact = float(ons.t[0]) + np.sqrt(np.einsum("ni,ij,nj->n", w, D, w))
+    np.testing.assert_allclose(ek["phi"][tet], exact[tet], rtol=1e-13)
+    assert np.all(ek["parent"][tet] == -1)
+    assert np.all(ek["phi"] >= exact - 1e-12)
+
+
+def test_unreached_component():
+    """Two disjoint cubes, onset in one: the other stays at +inf, flagged."""
+    a = S.kuhn_cube(4, 1.0)
+    b = S.kuhn_cube(4, 1.0)
+    xyz = np.concatenate([a.xyz, b.xyz + np.float32(5.0)])
+    tets = np.concatenate([a.tets, b.tets + a.n_v]).astype(np.int32)
+    mesh = S.Mesh(xyz, tets)
+    fib, cf, ct = uniform_params(mesh)
+    ons = S.Onsets(S.ONSET_NODAL, np.array([0], np.int32), np.array([1.0], np.float32))
+    ek = O.eikonal(mesh, fib, cf, ct, ons)
+    assert np.all(np.isfinite(ek["phi"][:a.n_v]))
+    assert np.all(np.isinf(ek["phi"][a.n_v:]))
+    assert np.all(ek["parent"][a.n_v:] == O.UNREACHED)
+    assert ek["stats"]["unreached"] == b.n_v
