@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Geodesic-BP benchmark: forward + gradient evaluations per second and
+tet-updates per second on the 72^3 Kuhn cube (373,248 vertices,
+2,147,466 tets), FP32 eikonal / ECG / adjoint on one GB300 per rank.
+
+One step = one forward-plus-gradient evaluation through the C ABI
+(gbp_forward_backward): per-tet metric precompute, onset seeding, the
+persistent FIM eikonal solve with parent record, the parent pass, the
+lead-field ECG (8 leads x 150 samples), the misfit and its phi-derivative,
+and the frozen-graph adjoint to per-tet c_f, c_t, onset times and positions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbp|reference]
+
+Under torchrun every rank runs an independent replica (the evaluation does
+not shard); value = all ranks' evaluations / max-over-ranks time.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Geodesic-BP fwd+grad evals/s at 2.15M tets (72^3 Kuhn cube, FP32)"
+BYTES_PER_TET_UPDATE = 92.0   # algorithmic bytes per local face update
+BYTES_PER_ADJ_NODE = 130.0    # algorithmic bytes per vertex of the adjoint
+
+
+def workload_config(n):
+    return {
+        "workload": f"Kuhn cube {n}^3 vertices (10 mm), per-node log c_f/c_t fields -> per-tet "
+                    "c (exp of vertex mean), depth-rotating fibres, 10 element onsets, 8 leads "
+                    "(P1 lead field, 1/r kernel, 30 mm sphere), T=150 @ 1 ms, misfit vs noisy target",
+        "n": n,
+    }
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.strip().split(",") for r in self.file.read().splitlines() if r.strip()]
+        try:
+            os.unlink(self.file.name)
+        except OSError:
+            pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_inputs(n, seed=0):
+    from paper_2308_08410_gb300 import synth as S
+    p = S.make_c3(n=n, seed=seed)
+    return p
+
+
+def run_cpu_oracle_eval(p, cf, ct, ons, target):
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    r = O.forward_backward(p.mesh, p.fib, cf, ct, ons, p.L, p.tmpl, target)
+    return time.perf_counter() - t0, r
+
+
+def eval_point(p):
+    """Parameters the benchmark evaluates at: the prior-mean initial guess of
+    the inverse problem (c_f = 0.6, c_t = 0.3 mm/ms, onset times 10 ms at the
+    true sites)."""
+    from paper_2308_08410_gb300 import synth as S
+    cf = np.full(p.mesh.n_t, 0.6, np.float32)
+    ct = np.full(p.mesh.n_t, 0.3, np.float32)
+    ons = S.Onsets(p.onsets.kind, p.onsets.idx, np.full(p.onsets.K, 10.0, np.float32), p.onsets.bary)
+    return cf, ct, ons
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gbp", "reference"], default="gbp")
+    ap.add_argument("--n", type=int, default=72, help="vertices per cube edge")
+    ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--local", choices=["exact", "fista"], default="exact")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 0)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, world)
+        return
+
+    import torch
+    from paper_2308_08410_gb300 import gbp
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    p = build_inputs(args.n)
+    ctx = gbp.Context(local_rank)
+    dp = gbp.setup_problem(ctx, p)
+    dev = ctx.torch_device
+    # target: the ECG of the seeded ground truth plus 5 % per-lead noise
+    phi_t, _, _ = ctx.eikonal_solve()
+    V_true = ctx.ecg_forward(phi_t, p.tmpl).cpu().numpy()
+    from paper_2308_08410_gb300 import synth as S
+    target_np = S.add_noise(V_true, 0.05, 4242)
+    target = torch.from_numpy(target_np).to(dev)
+    cf_np, ct_np, ons = eval_point(p)
+    cf = torch.from_numpy(cf_np).to(dev)
+    ct = torch.from_numpy(ct_np).to(dev)
+    t_on = torch.from_numpy(ons.t).to(dev)
+    opts = gbp.make_opts(local_solver=gbp.LOCAL_FISTA if args.local == "fista" else gbp.LOCAL_EXACT, n_f=32)
+    prec = gbp.PREC_BF16 if args.precision == "bf16" else gbp.PREC_FP32
+    out = None
+
+    def step():
+        nonlocal out
+        out = ctx.forward_backward(cf, ct, target, p.tmpl, t=t_on, opts=opts, precision=prec, out=out)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    if st["status"] != 0:
+        raise SystemExit(f"solve failed: {st}")
+
+    stream = torch.cuda.current_stream(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.enable_timing(True)
+    ctx.reset_kernel_times()
+    sampler = ClockSampler(local_rank)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = ctx.launch_count()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = ctx.launch_count() - launches0
+    clocks = sampler.stop()
+    ms_steps = [a.elapsed_time(b) for a, b in evs]
+    kt_ms, kt_n = ctx.kernel_times(6)
+    ctx.enable_timing(False)
+    st = ctx.stats()
+    total_s = sum(ms_steps) / 1e3
+    if dist is not None:
+        tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+        dist.barrier()
+
+    # e2e: the same evaluation from host buffers through gbp_forward_backward_host
+    e2e = None
+    if not args.no_e2e:
+        h_out = None
+        for _ in range(2):
+            h_out = ctx.forward_backward_host(cf_np, ct_np, target_np, p.tmpl, t=ons.t, opts=opts,
+                                              precision=prec, out=h_out)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            h_out = ctx.forward_backward_host(cf_np, ct_np, target_np, p.tmpl, t=ons.t, opts=opts,
+                                              precision=prec, out=h_out)
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        n_t, K, NT = p.mesh.n_t, p.onsets.K, target_np.size
+        e2e = {"value": world * args.steps / e2e_s, "unit": "evals/s",
+               "h2d_bytes_per_step": int(4 * (2 * n_t + K + NT)),
+               "d2h_bytes_per_step": int(4 * (1 + 2 * n_t + 4 * K))}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = measured_peaks()
+    steps = args.steps
+    fim_ms = kt_ms[0] / max(kt_n[0], 1)
+    adj_ms = kt_ms[4] / max(kt_n[4], 1)
+    face_updates = st["face_updates"]
+    achieved = face_updates * BYTES_PER_TET_UPDATE / (fim_ms / 1e3) / 1e9
+    adj_achieved = p.mesh.n_v * BYTES_PER_ADJ_NODE / (adj_ms / 1e3) / 1e9
+    ms_per_step = 1e3 * total_s / steps
+    value = world * steps / total_s
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        from oracle import oracle as O
+        t_cpu, r = run_cpu_oracle_eval(p, cf_np, ct_np, ons, target_np)
+        cpu = {"value": 1.0 / t_cpu, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": "one full evaluation of the same workload (FP64 oracle: worklist Gauss-Seidel "
+                         "eikonal single-threaded, ECG / misfit OpenMP, SCC adjoint serial)",
+               "seconds": t_cpu, "loss_gpu": float(out["loss"].item()), "loss_oracle": r["loss"]}
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "fim_traffic.json")
+    if os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                tj = json.load(f)
+            if tj.get("kernel_hash") == kernel_hash():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else "f32 eikonal/adjoint, bf16 ECG",
+        "data": "synthetic",
+        "config": dict(workload_config(args.n), n_v=p.mesh.n_v, n_t=p.mesh.n_t, leads=int(p.L.shape[0]),
+                       T=p.tmpl.T, onsets=p.onsets.K, local_solver=args.local, precision=args.precision,
+                       l2="flushed between steps (256 MB write)", parallelism="replicas"),
+        "tet_updates_per_s": world * face_updates * steps / total_s,
+        "fim": {"iterations": st["iterations"], "face_updates": face_updates, "candidates": st["candidates"],
+                "fp64_fallbacks": st["fp64_fallbacks"], "ms": fim_ms},
+        "adjoint": {"levels": st["adj_levels"], "cycle_nodes": st["adj_cycle_nodes"],
+                    "cycle_iters": st["adj_cycle_iters"], "ms": adj_ms,
+                    "roofline": {"bound": "hbm", "achieved": adj_achieved, "peak": peak, "unit": "GB/s",
+                                 "frac": adj_achieved / peak}},
+        "kernel_ms_per_step": {name: kt_ms[i] / steps for i, name in
+                               enumerate(["fim", "parent_pass", "ecg_fwd", "ecg_bwd", "adjoint", "precompute"])},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "k_fim",
+                     "peak_source": peak_kind},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("fim.cu", "gbp_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def run_reference(args, world):
+    """The FP64 CPU oracle, as it stands, on the host cores: each step is one
+    full evaluation of the same workload (about 12 s); warm-up steps are not
+    needed on the CPU and steps stop after ~150 s (the count is reported)."""
+    from oracle import oracle as O
+    p = build_inputs(args.n)
+    ek = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    from paper_2308_08410_gb300 import synth as S
+    target = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 4242)
+    cf, ct, ons = eval_point(p)
+    times = []
+    t_start = time.perf_counter()
+    for _ in range(max(1, args.steps)):
+        dt, _ = run_cpu_oracle_eval(p, cf, ct, ons, target)
+        times.append(dt)
+        if time.perf_counter() - t_start > 150:
+            break
+    total = sum(times)
+    value = len(times) / total
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "evals/s",
+        "n_gpus": world,
+        "steps": len(times),
+        "warmup": 0,
+        "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": dict(workload_config(args.n), n_v=p.mesh.n_v, n_t=p.mesh.n_t, leads=int(p.L.shape[0]),
+                       T=p.tmpl.T, onsets=p.onsets.K, parallelism="host cores"),
+        "cpu_baseline": {"value": value, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{len(times)} full evaluations of the workload (steps requested "
+                                   f"{args.steps}; capped near 150 s)"},
+        "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

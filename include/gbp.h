@@ -1,0 +1,244 @@
+/*
+ * gbp.h -- C ABI of the GB300 Geodesic-BP library (libgbp.so).
+ *
+ * One forward-plus-gradient evaluation of the eikonal ECG model of
+ * Grandits et al., "Digital twinning of cardiac electrophysiology models from
+ * the surface ECG: a geodesic backpropagation approach":
+ *
+ *   1. anisotropic eikonal solve on a P1 tetrahedral mesh (Eq. (1)) as the
+ *      discrete Hopf-Lax fixed point (Eq. hopflax_global, Eq. hopflax_local,
+ *      Algorithm 2), recording each vertex's minimising parent face and
+ *      barycentric point;
+ *   2. the lead-field ECG V = B U(t - phi) (Sec. II-D, Eq. tanh_waveform);
+ *   3. the gradient of the ECG misfit (Eq. inverse_ecg) with respect to the
+ *      conduction velocities and the onsets, taken along the frozen parent
+ *      graph (Sec. II-C, Eq. dto_grad, Eq. upwind_xi).
+ *
+ * Conventions
+ *   - Units: mm, ms, mm/ms.  Floating point is IEEE float32 unless stated.
+ *   - Conduction tensor of element j (Eq. (1)): M_j = ct_j^2 I +
+ *     (cf_j^2 - ct_j^2) f_j f_j^T with unit fibre f_j; the local metric is
+ *     D_j = M_j^{-1} (Sec. II-A).
+ *   - Parent code of vertex i: tet*4 + slot (slot = position of i in the tet);
+ *     the face E_{j\i} is the tet's other three vertices in increasing slot
+ *     order, and alpha[3] refers to that order.  A vertex holding its onset
+ *     value has code -1-k (onset k); an unreached vertex INT32_MIN and
+ *     phi = +inf.
+ *   - Pointer kinds are stated per argument: "device" pointers are CUDA
+ *     device memory of the context's device, "host" pointers are ordinary
+ *     (pageable or pinned) host memory.  Arrays are caller-owned; the library
+ *     never frees or retains them beyond the call unless stated.
+ *   - Calls are stream-ordered on the context stream and asynchronous unless
+ *     stated.  Errors: every call returns a gbp_status; argument errors are
+ *     detected on the host before any launch.  Device-side failures (a
+ *     bounded wait that ran out, an iteration limit) are latched into the
+ *     context and reported by the next synchronising call
+ *     (gbp_get_solve_stats, gbp_synchronize, the *_host calls).  The library
+ *     never aborts the process and never traps on the device.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef GBP_H
+#define GBP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbp_ctx gbp_ctx;
+
+typedef enum {
+    GBP_OK = 0,
+    GBP_ERR_INVALID_ARG = 1,   /* bad size, NULL pointer, out-of-range index */
+    GBP_ERR_BAD_MESH = 2,      /* inverted / degenerate tet, bad vertex id */
+    GBP_ERR_NOT_SPD = 3,       /* velocity <= 0 or not finite, zero fibre */
+    GBP_ERR_NOT_CONVERGED = 4, /* iteration limit reached */
+    GBP_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out */
+    GBP_ERR_UNREACHABLE = 6,   /* (informational) vertices left at +inf */
+    GBP_ERR_CUDA = 7,          /* CUDA runtime error */
+    GBP_ERR_STATE = 8,         /* call order violated (e.g. no mesh yet) */
+    GBP_ERR_NO_MEMORY = 9
+} gbp_status;
+
+enum { GBP_LOCAL_EXACT = 0, GBP_LOCAL_FISTA = 1 };
+enum { GBP_ONSET_NODAL = 0, GBP_ONSET_ELEMENT = 1 };
+enum { GBP_PREC_FP32 = 0, GBP_PREC_BF16 = 1 };
+
+/* Options of one eikonal solve (Algorithm 2). */
+typedef struct {
+    int32_t local_solver; /* GBP_LOCAL_EXACT: exact minimiser of Eq. (upwind_eq_lsqr);
+                             GBP_LOCAL_FISTA: Algorithm 1 with n_f steps */
+    int32_t n_f;          /* FISTA steps (ignored for EXACT); 1..256 */
+    float eps;            /* Algorithm 2's epsilon: a vertex re-activates its
+                             neighbours when it decreased by more than eps (ms);
+                             0 = on any decrease */
+    int32_t max_iters;    /* iteration limit; 0 = 8 * (cube root of n_v) + 64 + n_f */
+} gbp_solve_opts;
+
+/* Statistics of the last solve / backward pass (read by gbp_get_solve_stats). */
+typedef struct {
+    int64_t iterations;     /* FIM iterations (grid-wide steps) */
+    int64_t candidates;     /* vertex updates attempted */
+    int64_t face_updates;   /* local problems solved (faces with a changed vertex) */
+    int64_t fp64_fallbacks; /* local problems redone in FP64 */
+    int64_t unreached;      /* vertices left at +inf */
+    int64_t adj_levels;     /* adjoint: topological levels */
+    int64_t adj_cycle_nodes;/* adjoint: vertices solved by the cycle iteration */
+    int64_t adj_cycle_iters;/* adjoint: iterations of the cycle iteration */
+    int32_t status;         /* gbp_status of the last solve / backward */
+    int32_t reserved;
+} gbp_solve_stats;
+
+/* Template action potential (Eq. tanh_waveform), read as
+ * U(xi) = K0 + (K1 - K0)/2 (1 + tanh(2 xi / tau)), sampled at
+ * t_s = t0 + s dt, s = 0..T-1. */
+typedef struct {
+    float K0, K1, tau, t0, dt;
+    int32_t T;
+} gbp_template;
+
+/* ------------------------------------------------------------------ */
+/* context                                                              */
+/* ------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  `stream` is a cudaStream_t (or
+ * NULL for the legacy default stream); every call of this context is ordered
+ * on it.  *out receives the context (NULL on failure). */
+gbp_status gbp_create(gbp_ctx **out, int device, void *stream);
+void gbp_destroy(gbp_ctx *ctx);
+gbp_status gbp_set_stream(gbp_ctx *ctx, void *stream);
+const char *gbp_status_string(gbp_status s);
+/* Synchronise the context stream and report any latched device error. */
+gbp_status gbp_synchronize(gbp_ctx *ctx);
+
+/* ------------------------------------------------------------------ */
+/* problem set-up                                                       */
+/* ------------------------------------------------------------------ */
+
+/* Mesh of Sec. II-A: xyz host float32 [n_v][3], tets host int32 [n_t][4],
+ * positively oriented.  Validates (vertex ids in range and distinct, volume
+ * > 0), builds the vertex->tet and vertex->vertex adjacency on the host and
+ * uploads it.  Synchronous.  Errors: GBP_ERR_BAD_MESH, GBP_ERR_INVALID_ARG.
+ * Invalidates fibres, velocities, onsets, lead field and the last solve. */
+gbp_status gbp_upload_mesh(gbp_ctx *ctx, const float *xyz, int64_t n_v, const int32_t *tets,
+                           int64_t n_t);
+
+/* Fibre directions f_j: device float32 [n_t][3] (normalised here; a zero
+ * vector is GBP_ERR_NOT_SPD at the next velocity update). Copied. */
+gbp_status gbp_set_fibres(gbp_ctx *ctx, const float *fib);
+
+/* Velocities cf_j, ct_j: device float32 [n_t] each.  Copied, and the
+ * per-tet metric D_j = M_j^{-1} is precomputed on the device.  Invalid values
+ * (<= 0, NaN) are latched as GBP_ERR_NOT_SPD and reported by the next
+ * synchronising call.  Requires fibres. */
+gbp_status gbp_set_velocities(gbp_ctx *ctx, const float *cf, const float *ct);
+
+/* Lead-field operator B of Eq. (integral_potential_ecg), read as N x n_v
+ * (one row per lead): device float32 [N][n_v], 1 <= N <= 16.  Copied; the
+ * BF16 copy with per-lead scales is prepared here. */
+gbp_status gbp_set_leadfield(gbp_ctx *ctx, const float *L, int32_t N);
+
+/* Onsets X0 of Eq. (1).  kind GBP_ONSET_NODAL: idx = vertex ids, bary unused
+ * (may be NULL); GBP_ONSET_ELEMENT: idx = tet ids and bary = barycentric
+ * coordinates [K][4] of x_k in that tet (Eq. upwind_xi).  t = onset times.
+ * All device pointers: idx int32 [K], bary float32 [K][4], t float32 [K].
+ * 1 <= K <= 65536.  Copied.  Index range is checked on the device and
+ * latched as GBP_ERR_INVALID_ARG. */
+gbp_status gbp_set_onsets(gbp_ctx *ctx, int32_t kind, int32_t K, const int32_t *idx,
+                          const float *bary, const float *t);
+
+/* ------------------------------------------------------------------ */
+/* the hot path                                                         */
+/* ------------------------------------------------------------------ */
+
+/* Eikonal solve (Algorithm 2 with the local solver of Sec. II-B):
+ * persistent active-list FIM, then the parent pass.  Outputs (device, any
+ * may be NULL): phi float32 [n_v], parent int32 [n_v], alpha float32
+ * [n_v][3].  The context keeps its own copy of the parent graph for
+ * gbp_geodesic_backward.  Asynchronous; stats via gbp_get_solve_stats. */
+gbp_status gbp_eikonal_solve(gbp_ctx *ctx, const gbp_solve_opts *opts, float *phi,
+                             int32_t *parent, float *alpha);
+
+/* Synchronises and returns the statistics and status of the last solve and
+ * backward pass. */
+gbp_status gbp_get_solve_stats(gbp_ctx *ctx, gbp_solve_stats *stats);
+
+/* ECG V[l][s] = sum_n B[l][n] U(t_s - phi_n) (Sec. II-D).  phi device float32
+ * [n_v] (+inf allowed), ecg device float32 [N][T] (written).
+ * precision GBP_PREC_FP32 (CUDA cores) or GBP_PREC_BF16 (tensor cores:
+ * BF16 template values and per-lead-scaled BF16 lead field, FP32
+ * accumulation; the constant part of U is applied exactly in FP32).
+ * T <= 4096. */
+gbp_status gbp_ecg_forward(gbp_ctx *ctx, const float *phi, const gbp_template *tmpl,
+                           int32_t precision, float *ecg);
+
+/* Misfit of Eq. (inverse_ecg) with the rectangle rule,
+ * loss = 1/(N T) sum_{l,s} (ecg - target)^2, and its derivative with respect
+ * to each phi_n (Sec. II-D: nabla V = -B^T U' nabla phi).  phi, ecg (from
+ * gbp_ecg_forward), target device float32; loss device float32 [1];
+ * dphi device float32 [n_v]. */
+gbp_status gbp_ecg_loss_backward(gbp_ctx *ctx, const float *phi, const float *ecg,
+                                 const float *target, const gbp_template *tmpl, float *loss,
+                                 float *dphi);
+
+/* Frozen-graph adjoint of the last gbp_eikonal_solve (Sec. II-C, Eq.
+ * dto_grad, Eq. upwind_xi; the conduction-tensor variant of Sec. IV):
+ * mu = (I - P^T)^{-1} dphi, accumulated in reverse topological order of the
+ * parent graph (short cycles are resolved by a bounded fixed-point
+ * iteration).  dphi device float32 [n_v] (dLoss/dphi).  Outputs (device,
+ * written, any may be NULL): d_cf, d_ct float32 [n_t], d_t float32 [K],
+ * d_x float32 [K][3] (zero for nodal onsets).  GBP_ERR_STATE without a solve
+ * or after the parameters changed since it. */
+gbp_status gbp_geodesic_backward(gbp_ctx *ctx, const float *dphi, float *d_cf, float *d_ct,
+                                 float *d_t, float *d_x);
+
+/* One forward-plus-gradient evaluation: velocities -> eikonal -> ECG ->
+ * misfit -> adjoint.  cf, ct device float32 [n_t]; t device float32 [K]
+ * (NULL keeps the onset times of gbp_set_onsets); target device float32
+ * [N][T]; outputs device: loss [1], ecg [N][T] (may be NULL), d_cf, d_ct
+ * [n_t], d_t [K], d_x [K][3] (any may be NULL). */
+gbp_status gbp_forward_backward(gbp_ctx *ctx, const gbp_solve_opts *opts,
+                                const gbp_template *tmpl, int32_t precision, const float *cf,
+                                const float *ct, const float *t, const float *target, float *loss,
+                                float *ecg, float *d_cf, float *d_ct, float *d_t, float *d_x);
+
+/* The same evaluation from HOST buffers: inputs are copied host->device and
+ * outputs device->host inside the call, which synchronises.  cf, ct host
+ * [n_t]; t host [K] (NULL keeps the current times); target host [N][T];
+ * loss host [1]; d_cf, d_ct host [n_t]; d_t host [K]; d_x host [K][3]
+ * (outputs may be NULL).  Uses staging buffers owned by the context. */
+gbp_status gbp_forward_backward_host(gbp_ctx *ctx, const gbp_solve_opts *opts,
+                                     const gbp_template *tmpl, int32_t precision,
+                                     const float *cf, const float *ct, const float *t,
+                                     const float *target, float *loss, float *d_cf,
+                                     float *d_ct, float *d_t, float *d_x);
+
+/* ------------------------------------------------------------------ */
+/* diagnostics                                                          */
+/* ------------------------------------------------------------------ */
+
+/* The local problem of Eq. (upwind_eq_lsqr) on n independent faces (for
+ * tests): e device float32 [n][3][3] (rows v_{j_m} - v_i), fib [n][3],
+ * cf, ct [n], Phi [n][3] (+inf allowed); mode GBP_LOCAL_EXACT or
+ * GBP_LOCAL_FISTA (Algorithm 1, n_f steps, Lipschitz constant of Eq.
+ * (lipschitz_est) with h_ = h_min / 1.1).  Writes value [n], alpha [n][3]. */
+gbp_status gbp_local_solve_batch(gbp_ctx *ctx, int64_t n, const float *e, const float *fib,
+                                 const float *cf, const float *ct, const float *Phi,
+                                 int32_t mode, int32_t n_f, float *value, float *alpha);
+
+/* Kernel timing: when enabled, the library records CUDA events around its
+ * main kernels on the context stream.  gbp_get_kernel_times synchronises and
+ * returns, per kernel class (0 eikonal FIM, 1 parent pass, 2 ECG forward,
+ * 3 ECG backward, 4 adjoint, 5 set-up/precompute), the summed milliseconds
+ * and launch counts since the last reset.  n_classes <= 8. */
+gbp_status gbp_enable_timing(gbp_ctx *ctx, int32_t on);
+gbp_status gbp_get_kernel_times(gbp_ctx *ctx, int32_t n_classes, double *ms, int64_t *launches);
+gbp_status gbp_reset_kernel_times(gbp_ctx *ctx);
+/* Total kernels this context launched since creation. */
+int64_t gbp_launch_count(gbp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBP_H */

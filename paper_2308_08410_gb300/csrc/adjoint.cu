@@ -1,0 +1,362 @@
+// adjoint.cu -- Geodesic-BP gradient along the frozen parent graph
+// (Sec. II-C, Eq. dto_grad, Eq. upwind_xi; velocities as in the
+// conduction-tensor remark of Sec. IV).
+//
+// For a vertex i with face parent (j, slot) and barycentric alpha:
+//   phi_i = sum_n alpha_n phi_{j_n} + ||w||_{D_j},  w = v_i - sum_n alpha_n v_{j_n},
+// alpha frozen (first variation), so d phi_i / d phi_{j_n} = alpha_n and,
+// with ||w||_D^2 = |w_perp|^2 / ct^2 + (f.w)^2 / cf^2,
+//   d phi_i / d cf_j = -(f.w)^2 / (cf^3 ||w||_D),
+//   d phi_i / d ct_j = -|w_perp|^2 / (ct^3 ||w||_D).
+// Onset vertices: d phi / d t_k = 1; element onsets (Eq. upwind_xi) add
+// d phi_v / d x_k = -D_E (v - x_k) / ||v - x_k||_{D_E} and the velocity
+// derivatives of tet E with w = v - x_k.
+//
+// mu = (I - P^T)^{-1} dL/dphi is accumulated children-first: a vertex is
+// processed once every child (vertex whose parent face holds it with
+// alpha > 0) has pushed alpha * mu into it (topological levels, one grid
+// barrier per level).  The parent graph of the discrete fixed point can hold
+// short cycles (non-causal updates in anisotropic elements); the vertices
+// they block are finished by a bounded fixed-point (Jacobi) iteration on the
+// remaining sub-graph, which is closed under taking parents.
+#include "gbp_internal.cuh"
+
+namespace gbp {
+
+struct AdjArgs {
+    int64_t n_v;
+    const float4 *xyz;
+    const int4 *tets;
+    const float4 *tm;
+    const float *tsd;
+    const float *cf, *ct;
+    const int4 *rec;
+    int onset_kind;
+    const int *on_idx;
+    const float *on_bary;
+    float *mu, *xj, *acc;
+    int *cnt, *proc, *lists;
+    float *d_cf, *d_ct, *d_t, *d_x;
+    Control *ctl;
+    int max_cycle_iters;
+};
+
+__device__ __forceinline__ void velocity_terms(float3 w, float4 m, float cfj, float ctj, float mu, float *d_cf,
+                                               float *d_ct, int j)
+{
+    float fw = m.x * w.x + m.y * w.y + m.z * w.z;
+    float3 wp = make_float3(w.x - fw * m.x, w.y - fw * m.y, w.z - fw * m.z);
+    float wp2 = f3dot(wp, wp);
+    float icf = 1.f / cfj, ict = 1.f / ctj;
+    float g = sqrtf(wp2 * ict * ict + fw * fw * icf * icf);
+    if (!(g > 0.f)) return;
+    float ig = 1.f / g;
+    if (d_cf) atomicAdd(&d_cf[j], -mu * fw * fw * icf * icf * icf * ig);
+    if (d_ct) atomicAdd(&d_ct[j], -mu * wp2 * ict * ict * ict * ig);
+}
+
+// gradient contributions of vertex i's own parent (no pushes)
+__device__ __forceinline__ void local_terms(const AdjArgs &a, int64_t i, int4 r, float m)
+{
+    const int code = r.x;
+    if (code >= 0) {
+        const int j = code >> 2, s = code & 3;
+        const int4 tv = __ldg(&a.tets[j]);
+        int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+        const float4 xi = __ldg(&a.xyz[i]);
+        const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
+        // w = v_i - sum alpha_n v_n = -sum alpha_n (v_n - v_i)
+        float3 w = make_float3(0.f, 0.f, 0.f);
+        int q3 = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (q == s) continue;
+            float4 xq = __ldg(&a.xyz[ids[q]]);
+            w.x = fmaf(-al[q3], xq.x - xi.x, w.x);
+            w.y = fmaf(-al[q3], xq.y - xi.y, w.y);
+            w.z = fmaf(-al[q3], xq.z - xi.z, w.z);
+            ++q3;
+        }
+        velocity_terms(w, __ldg(&a.tm[j]), __ldg(&a.cf[j]), __ldg(&a.ct[j]), m, a.d_cf, a.d_ct, j);
+    } else if (code != GBP_UNREACHED) {
+        const int k = -1 - code;
+        if (a.d_t) atomicAdd(&a.d_t[k], m);
+        if (a.onset_kind == GBP_ONSET_ELEMENT) {
+            const int E = __ldg(&a.on_idx[k]);
+            const int4 tv = __ldg(&a.tets[E]);
+            int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+            const float4 xi = __ldg(&a.xyz[i]);
+            // w = v - x_k = sum_q b_q (v - v_q)
+            float3 w = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float b = __ldg(&a.on_bary[4 * k + q]);
+                float4 xq = __ldg(&a.xyz[ids[q]]);
+                w.x = fmaf(b, xi.x - xq.x, w.x);
+                w.y = fmaf(b, xi.y - xq.y, w.y);
+                w.z = fmaf(b, xi.z - xq.z, w.z);
+            }
+            const float4 mm = __ldg(&a.tm[E]);
+            const float cfe = __ldg(&a.cf[E]), cte = __ldg(&a.ct[E]);
+            float fw = mm.x * w.x + mm.y * w.y + mm.z * w.z;
+            float3 wp = make_float3(w.x - fw * mm.x, w.y - fw * mm.y, w.z - fw * mm.z);
+            float icf = 1.f / cfe, ict = 1.f / cte;
+            float g = sqrtf(f3dot(wp, wp) * ict * ict + fw * fw * icf * icf);
+            if (g > 0.f) {
+                // D w = wp / ct^2 + (f.w) f / cf^2
+                float ig = 1.f / g;
+                if (a.d_x) {
+                    float c1 = ict * ict, c2 = fw * icf * icf;
+                    atomicAdd(&a.d_x[3 * k + 0], -m * (wp.x * c1 + c2 * mm.x) * ig);
+                    atomicAdd(&a.d_x[3 * k + 1], -m * (wp.y * c1 + c2 * mm.y) * ig);
+                    atomicAdd(&a.d_x[3 * k + 2], -m * (wp.z * c1 + c2 * mm.z) * ig);
+                }
+                velocity_terms(w, mm, cfe, cte, m, a.d_cf, a.d_ct, E);
+            }
+        }
+    }
+}
+
+__global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const float *__restrict__ dphi, float *mu,
+                           int *cnt, int *proc, Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_v) return;
+    bool reached = rec[i].x != GBP_UNREACHED;
+    mu[i] = reached ? dphi[i] : 0.f;
+    cnt[i] = 0;
+    proc[i] = reached ? 0 : 1;
+}
+
+__global__ void k_adj_count(int64_t n_v, const int4 *__restrict__ rec, const int4 *__restrict__ tets, int *cnt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_v) return;
+    int4 r = rec[i];
+    if (r.x < 0) return;
+    int j = r.x >> 2, s = r.x & 3;
+    int4 tv = tets[j];
+    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+    int al[3] = {r.y, r.z, r.w};
+    int q3 = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (q == s) continue;
+        if (__int_as_float(al[q3]) != 0.f) atomicAdd(&cnt[ids[q]], 1);
+        ++q3;
+    }
+}
+
+__global__ void k_adj_seed(int64_t n_v, const int *__restrict__ cnt, const int *__restrict__ proc, int *list1,
+                           Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool app = i < n_v && proc[i] == 0 && cnt[i] == 0;
+    warp_append(app, (int)i, list1, &ctl->count[1]);
+}
+
+__device__ __forceinline__ float ld_cg_f(const float *p) { return __ldcg(p); }
+
+__global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
+{
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n_v = a.n_v;
+    unsigned int nbar = 0;
+    __shared__ int s_proc;
+    if (threadIdx.x == 0) s_proc = 0;
+    __syncthreads();
+    int levels = 0;
+    bool ok = true;
+    // ---- topological levels ----
+    for (int k = 1;; ++k) {
+        const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
+        const int n_cur = ld_relaxed_i32(&a.ctl->count[cur]);
+        if (n_cur == 0) break;
+        ++levels;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->count[nn] = 0;
+        const int *list = a.lists + (int64_t)cur * n_v;
+        int *nlist = a.lists + (int64_t)nxt * n_v;
+        int mine = 0;
+        for (int64_t base = 0; base < n_cur; base += nth) {
+            const int64_t w = base + tid;
+            bool app[3] = {false, false, false};
+            int vv[3] = {0, 0, 0};
+            if (w < n_cur) {
+                const int i = __ldcg(&list[w]);
+                const float m = ld_cg_f(&a.mu[i]);
+                const int4 r = __ldg(&a.rec[i]);
+                a.proc[i] = 1;
+                ++mine;
+                local_terms(a, i, r, m);
+                if (r.x >= 0) {
+                    const int j = r.x >> 2, s = r.x & 3;
+                    const int4 tv = __ldg(&a.tets[j]);
+                    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+                    const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
+                    int q3 = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q == s) continue;
+                        if (al[q3] != 0.f) {
+                            const int v = ids[q];
+                            atomicAdd(&a.mu[v], al[q3] * m);
+                            __threadfence();
+                            if (atomicSub(&a.cnt[v], 1) == 1) {
+                                app[q3] = true;
+                                vv[q3] = v;
+                            }
+                        }
+                        ++q3;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) warp_append(app[q], vv[q], nlist, &a.ctl->count[nxt]);
+        }
+        if (mine) atomicAdd(&s_proc, mine);
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar * gridDim.x)) {
+            ok = false;
+            break;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_proc) atomicAdd(&a.ctl->adj_processed, s_proc);
+    if (!ok) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->adj_levels = levels;
+    // ---- vertices blocked by cycles: fixed-point iteration ----
+    // collect the unprocessed reached vertices R (closed under parents); the
+    // last level barrier ordered every write of the level loop before this
+    int *R = a.lists;  // no list is live any more
+    for (int64_t base = 0; base < n_v; base += nth) {
+        const int64_t i = base + tid;
+        bool app = i < n_v && __ldcg(&a.proc[i]) == 0;
+        if (app) {
+            a.xj[i] = ld_cg_f(&a.mu[i]);
+            a.acc[i] = 0.f;
+        }
+        warp_append(app, (int)i, R, &a.ctl->count[3]);
+    }
+    ++nbar;
+    if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
+    const int nR = ld_relaxed_i32(&a.ctl->count[3]);
+    if (nR == 0) return;
+    // x <- base + P_R^T x, base = mu (lam + pushes of processed children)
+    int it = 0;
+    for (; it < a.max_cycle_iters; ++it) {
+        for (int64_t w = tid; w < nR; w += nth) {
+            const int i = __ldcg(&R[w]);
+            const int4 r = __ldg(&a.rec[i]);
+            if (r.x < 0) continue;
+            const float x = ld_cg_f(&a.xj[i]);
+            const int j = r.x >> 2, s = r.x & 3;
+            const int4 tv = __ldg(&a.tets[j]);
+            int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+            const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
+            int q3 = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q == s) continue;
+                if (al[q3] != 0.f) atomicAdd(&a.acc[ids[q]], al[q3] * x);
+                ++q3;
+            }
+        }
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
+        // slot (it+1)&1 was last read before this iteration's first barrier
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->adj_delta[(it + 1) & 1] = 0.f;
+        float dmax = 0.f, xmax = 0.f;
+        for (int64_t w = tid; w < nR; w += nth) {
+            const int i = __ldcg(&R[w]);
+            const float xn = ld_cg_f(&a.mu[i]) + ld_cg_f(&a.acc[i]);
+            const float xo = ld_cg_f(&a.xj[i]);
+            dmax = fmaxf(dmax, fabsf(xn - xo));
+            xmax = fmaxf(xmax, fabsf(xn));
+            a.xj[i] = xn;
+            a.acc[i] = 0.f;
+        }
+        // converged when no entry moved by more than 1e-7 of its own size
+        float crit = dmax - 1e-7f * xmax;
+        if (crit > 0.f) atomicMax((int *)&a.ctl->adj_delta[it & 1], __float_as_int(crit));
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
+        if (__int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_delta[it & 1])) <= 0.f) {
+            ++it;
+            break;
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->adj_cycle_nodes = nR;
+        a.ctl->adj_cycle_iters = it;
+        if (it >= a.max_cycle_iters) atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_NOT_CONVERGED);
+    }
+    for (int64_t w = tid; w < nR; w += nth) {
+        const int i = __ldcg(&R[w]);
+        const float x = ld_cg_f(&a.xj[i]);
+        a.mu[i] = x;
+        a.proc[i] = 1;
+        local_terms(a, i, __ldg(&a.rec[i]), x);
+    }
+}
+
+cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_ct, float *d_t, float *d_x)
+{
+    cudaError_t err;
+    const int64_t n_v = c->n_v;
+    // keep the solve's statistics, reset the adjoint counters
+    err = cudaMemsetAsync(c->ctl->count, 0, sizeof(int) * 4, c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(&c->ctl->barrier, 0, sizeof(unsigned int) * 2, c->stream);  // barrier, abort
+    if (err) return err;
+    err = cudaMemsetAsync(&c->ctl->adj_levels, 0, sizeof(int) * 4 + 2 * sizeof(float), c->stream);
+    if (err) return err;
+    if (d_cf) cudaMemsetAsync(d_cf, 0, sizeof(float) * c->n_t, c->stream);
+    if (d_ct) cudaMemsetAsync(d_ct, 0, sizeof(float) * c->n_t, c->stream);
+    if (d_t) cudaMemsetAsync(d_t, 0, sizeof(float) * c->K, c->stream);
+    if (d_x) cudaMemsetAsync(d_x, 0, sizeof(float) * 3 * c->K, c->stream);
+    int th = 256;
+    unsigned bl = (unsigned)((n_v + th - 1) / th);
+    time_begin(c, 4);
+    k_adj_init<<<bl, th, 0, c->stream>>>(n_v, c->rec, dphi, c->mu, c->cnt, c->proc, c->ctl);
+    k_adj_count<<<bl, th, 0, c->stream>>>(n_v, c->rec, c->tets, c->cnt);
+    k_adj_seed<<<bl, th, 0, c->stream>>>(n_v, c->cnt, c->proc, c->lists + n_v, c->ctl);
+    c->launches += 3;
+    if ((err = cudaGetLastError())) return err;
+    AdjArgs a;
+    a.n_v = n_v;
+    a.xyz = c->xyz;
+    a.tets = c->tets;
+    a.tm = c->tm;
+    a.tsd = c->tsd;
+    a.cf = c->cf;
+    a.ct = c->ct;
+    a.rec = c->rec;
+    a.onset_kind = c->onset_kind;
+    a.on_idx = c->on_idx;
+    a.on_bary = c->on_bary;
+    a.mu = c->mu;
+    a.xj = c->jac_x;
+    a.acc = c->jac_acc;
+    a.cnt = c->cnt;
+    a.proc = c->proc;
+    a.lists = c->lists;
+    a.d_cf = d_cf;
+    a.d_ct = d_ct;
+    a.d_t = d_t;
+    a.d_x = d_x;
+    a.ctl = c->ctl;
+    a.max_cycle_iters = 4096;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    int grid = per_sm * c->num_sms;
+    void *args[] = {&a};
+    err = cudaLaunchCooperativeKernel((const void *)k_adjoint, dim3(grid), dim3(256), args, 0, c->stream);
+    time_end(c, 4);
+    c->launches++;
+    return err;
+}
+
+}  // namespace gbp

@@ -1,0 +1,652 @@
+// api.cu -- the C ABI of libgbp: context, problem set-up (mesh validation and
+// adjacency on the host, once per mesh), and the entry points of the hot path.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "gbp_internal.cuh"
+
+using gbp::Control;
+
+namespace {
+
+gbp_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return GBP_OK;
+    if (e == cudaErrorMemoryAllocation) return GBP_ERR_NO_MEMORY;
+    return GBP_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, int64_t n)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (n <= 0) n = 1;
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)n);
+}
+
+template <class T>
+void dfree(T **p)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void free_mesh_buffers(gbp_ctx *c)
+{
+    dfree(&c->xyz);
+    dfree(&c->tets);
+    dfree(&c->n2t_ptr);
+    dfree(&c->n2t);
+    dfree(&c->n2n_ptr);
+    dfree(&c->n2n);
+    dfree(&c->fib);
+    dfree(&c->cf);
+    dfree(&c->ct);
+    dfree(&c->tm);
+    dfree(&c->tsd);
+    dfree(&c->tlip);
+    dfree(&c->phi);
+    dfree(&c->rec);
+    dfree(&c->chg);
+    dfree(&c->stamp);
+    dfree(&c->lists);
+    dfree(&c->keys);
+    dfree(&c->mu);
+    dfree(&c->jac_x);
+    dfree(&c->jac_acc);
+    dfree(&c->cnt);
+    dfree(&c->proc);
+    dfree(&c->L);
+    dfree(&c->Lbf);
+    dfree(&c->Lscale);
+    dfree(&c->Lrowsum);
+    dfree(&c->on_idx);
+    dfree(&c->on_bary);
+    dfree(&c->on_t);
+    dfree(&c->dphi);
+    c->has_fib = c->has_vel = c->lip_valid = false;
+    c->N = 0;
+    c->K = 0;
+    c->solve_gen = -1;
+}
+
+gbp_status latched(gbp_ctx *c)
+{
+    // synchronise and read the device status word
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e) return from_cuda(e);
+    e = cudaMemcpy(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost);
+    if (e) return from_cuda(e);
+    return (gbp_status)(c->h_ctl->status ? c->h_ctl->status : c->h_ctl->param_status);
+}
+
+__global__ void k_rowsum(int64_t n_v, const float *__restrict__ L, float *__restrict__ rowsum)
+{
+    __shared__ double red[32];
+    const float *Ll = L + (int64_t)blockIdx.x * n_v;
+    double acc = 0.0;
+    for (int64_t n = threadIdx.x; n < n_v; n += blockDim.x) acc += (double)Ll[n];
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (threadIdx.x == 0) rowsum[blockIdx.x] = (float)v;
+    }
+}
+
+bool valid_template(const gbp_template *t)
+{
+    return t && t->T >= 1 && t->T <= 4096 && t->tau > 0.f && std::isfinite(t->tau) && t->dt > 0.f &&
+           std::isfinite(t->dt) && std::isfinite(t->t0) && std::isfinite(t->K0) && std::isfinite(t->K1);
+}
+
+}  // namespace
+
+namespace gbp {
+void flush_timing(gbp_ctx *c)
+{
+    if (c->ev_used == 0) return;
+    cudaStreamSynchronize(c->stream);
+    for (int p = 0; p + 1 < c->ev_used; p += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->ev_pool[p], c->ev_pool[p + 1]) == cudaSuccess) {
+            c->ms[c->ev_cls[p / 2]] += ms;
+            c->cls_launches[c->ev_cls[p / 2]] += 1;
+        }
+    }
+    c->ev_used = 0;
+}
+
+void time_begin(gbp_ctx *c, int cls)
+{
+    if (!c->timing) return;
+    if (c->ev_used + 2 > 64) flush_timing(c);
+    c->ev_cls[c->ev_used / 2] = cls;
+    cudaEventRecord(c->ev_pool[c->ev_used], c->stream);
+}
+
+void time_end(gbp_ctx *c, int cls)
+{
+    (void)cls;
+    if (!c->timing) return;
+    cudaEventRecord(c->ev_pool[c->ev_used + 1], c->stream);
+    c->ev_used += 2;
+}
+}  // namespace gbp
+
+extern "C" {
+
+const char *gbp_status_string(gbp_status s)
+{
+    switch (s) {
+    case GBP_OK: return "ok";
+    case GBP_ERR_INVALID_ARG: return "invalid argument";
+    case GBP_ERR_BAD_MESH: return "bad mesh (inverted or degenerate tetrahedron, bad vertex id)";
+    case GBP_ERR_NOT_SPD: return "conduction tensor not SPD (velocity <= 0 / not finite, zero fibre)";
+    case GBP_ERR_NOT_CONVERGED: return "iteration limit reached";
+    case GBP_ERR_TIMEOUT: return "bounded device wait ran out";
+    case GBP_ERR_UNREACHABLE: return "vertices unreachable from the onsets";
+    case GBP_ERR_CUDA: return "CUDA runtime error";
+    case GBP_ERR_STATE: return "call order violated";
+    case GBP_ERR_NO_MEMORY: return "out of device memory";
+    }
+    return "unknown status";
+}
+
+gbp_status gbp_create(gbp_ctx **out, int device, void *stream)
+{
+    if (!out) return GBP_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(device);
+    gbp_ctx *c = new gbp_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)stream;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    cudaError_t e = cudaMalloc(&c->ctl, sizeof(Control));
+    if (!e) e = cudaMemset(c->ctl, 0, sizeof(Control));
+    if (!e) e = cudaMallocHost(&c->h_ctl, sizeof(Control));
+    for (int i = 0; i < 64 && !e; ++i) e = cudaEventCreate(&c->ev_pool[i]);
+    if (e || !coop) {
+        gbp_destroy(c);
+        return e ? from_cuda(e) : GBP_ERR_CUDA;
+    }
+    *out = c;
+    return GBP_OK;
+}
+
+void gbp_destroy(gbp_ctx *c)
+{
+    if (!c) return;
+    DeviceGuard g(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_mesh_buffers(c);
+    dfree(&c->ctl);
+    dfree(&c->ecg_part);
+    dfree(&c->resid);
+    dfree(&c->ecg_tmp);
+    dfree(&c->dev_in);
+    dfree(&c->dev_out);
+    dfree(&c->loss_buf);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
+    if (c->pin_in) cudaFreeHost(c->pin_in);
+    if (c->pin_out) cudaFreeHost(c->pin_out);
+    for (int i = 0; i < 64; ++i)
+        if (c->ev_pool[i]) cudaEventDestroy(c->ev_pool[i]);
+    delete c;
+}
+
+gbp_status gbp_set_stream(gbp_ctx *c, void *stream)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    c->stream = (cudaStream_t)stream;
+    return GBP_OK;
+}
+
+gbp_status gbp_synchronize(gbp_ctx *c)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    return latched(c);
+}
+
+gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
+{
+    if (!c || !xyz || !tets || n_v < 4 || n_t < 1 || n_v >= (1ll << 30) || n_t >= (1ll << 29))
+        return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    // validation: ids in range and distinct, positive volume
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = 0; i < n_v; ++i)
+        for (int r = 0; r < 3; ++r) {
+            double v = xyz[3 * i + r];
+            if (!std::isfinite(v)) return GBP_ERR_BAD_MESH;
+            lo[r] = std::min(lo[r], v);
+            hi[r] = std::max(hi[r], v);
+        }
+    double diag = std::sqrt((hi[0] - lo[0]) * (hi[0] - lo[0]) + (hi[1] - lo[1]) * (hi[1] - lo[1]) +
+                            (hi[2] - lo[2]) * (hi[2] - lo[2]));
+    double vtol = 1e-15 * diag * diag * diag;
+    for (int64_t j = 0; j < n_t; ++j) {
+        const int32_t *t = tets + 4 * j;
+        for (int q = 0; q < 4; ++q)
+            if (t[q] < 0 || t[q] >= n_v) return GBP_ERR_BAD_MESH;
+        for (int a = 0; a < 4; ++a)
+            for (int b = a + 1; b < 4; ++b)
+                if (t[a] == t[b]) return GBP_ERR_BAD_MESH;
+        double e[3][3];
+        for (int a = 0; a < 3; ++a)
+            for (int r = 0; r < 3; ++r) e[a][r] = (double)xyz[3 * t[a + 1] + r] - (double)xyz[3 * t[0] + r];
+        double det = e[0][0] * (e[1][1] * e[2][2] - e[1][2] * e[2][1]) - e[0][1] * (e[1][0] * e[2][2] - e[1][2] * e[2][0]) +
+                     e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
+        if (!(det / 6.0 > vtol)) return GBP_ERR_BAD_MESH;
+    }
+    // vertex -> (tet*4 + slot), rows sorted
+    std::vector<int> n2t_ptr(n_v + 1, 0), n2t(4 * n_t);
+    for (int64_t j = 0; j < n_t; ++j)
+        for (int q = 0; q < 4; ++q) n2t_ptr[tets[4 * j + q] + 1]++;
+    for (int64_t i = 0; i < n_v; ++i) n2t_ptr[i + 1] += n2t_ptr[i];
+    {
+        std::vector<int> cur(n2t_ptr.begin(), n2t_ptr.end() - 1);
+        for (int64_t j = 0; j < n_t; ++j)
+            for (int q = 0; q < 4; ++q) n2t[cur[tets[4 * j + q]]++] = (int)(4 * j + q);
+    }
+    int max_deg = 0;
+    // vertex -> vertex (neighbours through a shared tet)
+    std::vector<int> n2n_ptr(n_v + 1, 0), n2n;
+    n2n.reserve((size_t)n_t * 3);
+    std::vector<int> buf;
+    for (int64_t i = 0; i < n_v; ++i) {
+        int b = n2t_ptr[i], e = n2t_ptr[i + 1];
+        max_deg = std::max(max_deg, e - b);
+        buf.clear();
+        for (int p = b; p < e; ++p) {
+            int j = n2t[p] >> 2;
+            for (int q = 0; q < 4; ++q) {
+                int v = tets[4 * (int64_t)j + q];
+                if (v != i) buf.push_back(v);
+            }
+        }
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+        n2n.insert(n2n.end(), buf.begin(), buf.end());
+        n2n_ptr[i + 1] = (int)n2n.size();
+    }
+    free_mesh_buffers(c);
+    c->n_v = n_v;
+    c->n_t = n_t;
+    c->max_deg = max_deg;
+    std::vector<float4> x4(n_v);
+    for (int64_t i = 0; i < n_v; ++i) x4[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
+    cudaError_t err = cudaSuccess;
+#define CK(x)                                \
+    do {                                     \
+        if (!err) err = (x);                 \
+    } while (0)
+    CK(dalloc(&c->xyz, n_v));
+    CK(dalloc(&c->tets, n_t));
+    CK(dalloc(&c->n2t_ptr, n_v + 1));
+    CK(dalloc(&c->n2t, 4 * n_t));
+    CK(dalloc(&c->n2n_ptr, n_v + 1));
+    CK(dalloc(&c->n2n, (int64_t)n2n.size()));
+    CK(dalloc(&c->fib, 3 * n_t));
+    CK(dalloc(&c->cf, n_t));
+    CK(dalloc(&c->ct, n_t));
+    CK(dalloc(&c->tm, n_t));
+    CK(dalloc(&c->tsd, n_t));
+    CK(dalloc(&c->tlip, n_t));
+    CK(dalloc(&c->phi, n_v));
+    CK(dalloc(&c->rec, n_v));
+    CK(dalloc(&c->chg, n_v));
+    CK(dalloc(&c->stamp, n_v));
+    CK(dalloc(&c->lists, 3 * n_v + 32));
+    CK(dalloc(&c->keys, n_v));
+    CK(dalloc(&c->mu, n_v));
+    CK(dalloc(&c->jac_x, n_v));
+    CK(dalloc(&c->jac_acc, n_v));
+    CK(dalloc(&c->cnt, n_v));
+    CK(dalloc(&c->proc, n_v));
+    CK(dalloc(&c->dphi, n_v));
+    CK(cudaMemcpy(c->xyz, x4.data(), sizeof(float4) * n_v, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->tets, tets, sizeof(int4) * n_t, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2t_ptr, n2t_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2t, n2t.data(), sizeof(int) * 4 * n_t, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2n_ptr, n2n_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2n, n2n.data(), sizeof(int) * n2n.size(), cudaMemcpyHostToDevice));
+#undef CK
+    if (err) {
+        free_mesh_buffers(c);
+        c->n_v = c->n_t = 0;
+        return from_cuda(err);
+    }
+    c->param_gen++;
+    return GBP_OK;
+}
+
+gbp_status gbp_set_fibres(gbp_ctx *c, const float *fib)
+{
+    if (!c || !fib) return GBP_ERR_INVALID_ARG;
+    if (!c->n_t) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaMemcpyAsync(c->fib, fib, sizeof(float) * 3 * c->n_t, cudaMemcpyDeviceToDevice, c->stream);
+    if (e) return from_cuda(e);
+    c->has_fib = true;
+    c->has_vel = false;
+    c->lip_valid = false;
+    c->param_gen++;
+    return GBP_OK;
+}
+
+gbp_status gbp_set_velocities(gbp_ctx *c, const float *cf, const float *ct)
+{
+    if (!c || !cf || !ct) return GBP_ERR_INVALID_ARG;
+    if (!c->n_t || !c->has_fib) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaSuccess;
+    if (cf != c->cf) e = cudaMemcpyAsync(c->cf, cf, sizeof(float) * c->n_t, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e && ct != c->ct)
+        e = cudaMemcpyAsync(c->ct, ct, sizeof(float) * c->n_t, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e) e = cudaMemsetAsync(&c->ctl->param_status, 0, sizeof(int), c->stream);
+    if (!e) {
+        gbp::time_begin(c, 5);
+        e = gbp::launch_precompute(c);
+        gbp::time_end(c, 5);
+    }
+    if (e) return from_cuda(e);
+    c->has_vel = true;
+    c->lip_valid = false;
+    c->param_gen++;
+    return GBP_OK;
+}
+
+gbp_status gbp_set_leadfield(gbp_ctx *c, const float *L, int32_t N)
+{
+    if (!c || !L || N < 1 || N > 16) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaError_t e = dalloc(&c->L, (int64_t)N * c->n_v);
+    if (!e) e = dalloc(&c->Lrowsum, 16);
+    if (!e) e = cudaMemcpyAsync(c->L, L, sizeof(float) * N * c->n_v, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e) {
+        k_rowsum<<<N, 256, 0, c->stream>>>(c->n_v, c->L, c->Lrowsum);
+        c->launches++;
+        e = cudaGetLastError();
+    }
+    if (e) return from_cuda(e);
+    c->N = N;
+    e = gbp::prepare_leadfield_bf16(c);
+    return from_cuda(e);
+}
+
+gbp_status gbp_set_onsets(gbp_ctx *c, int32_t kind, int32_t K, const int32_t *idx, const float *bary,
+                          const float *t)
+{
+    if (!c || !idx || !t || K < 1 || K > 65536) return GBP_ERR_INVALID_ARG;
+    if (kind != GBP_ONSET_NODAL && kind != GBP_ONSET_ELEMENT) return GBP_ERR_INVALID_ARG;
+    if (kind == GBP_ONSET_ELEMENT && !bary) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaSuccess;
+    if (K != c->K) {
+        e = dalloc(&c->on_idx, K);
+        if (!e) e = dalloc(&c->on_bary, 4 * K);
+        if (!e) e = dalloc(&c->on_t, K);
+    }
+    if (!e) e = cudaMemcpyAsync(c->on_idx, idx, sizeof(int) * K, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e && kind == GBP_ONSET_ELEMENT)
+        e = cudaMemcpyAsync(c->on_bary, bary, sizeof(float) * 4 * K, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e && kind == GBP_ONSET_NODAL) e = cudaMemsetAsync(c->on_bary, 0, sizeof(float) * 4 * K, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * K, cudaMemcpyDeviceToDevice, c->stream);
+    if (e) return from_cuda(e);
+    c->K = K;
+    c->onset_kind = kind;
+    c->param_gen++;
+    return GBP_OK;
+}
+
+static gbp_solve_opts normalized_opts(const gbp_ctx *c, const gbp_solve_opts *o)
+{
+    gbp_solve_opts r;
+    if (o) r = *o;
+    else {
+        r.local_solver = GBP_LOCAL_EXACT;
+        r.n_f = 32;
+        r.eps = 0.f;
+        r.max_iters = 0;
+    }
+    if (r.max_iters <= 0) r.max_iters = (int)(8.0 * std::cbrt((double)c->n_v)) + 64 + r.n_f;
+    return r;
+}
+
+gbp_status gbp_eikonal_solve(gbp_ctx *c, const gbp_solve_opts *opts, float *phi, int32_t *parent, float *alpha)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v || !c->has_vel || !c->K) return GBP_ERR_STATE;
+    gbp_solve_opts o = normalized_opts(c, opts);
+    if (o.local_solver != GBP_LOCAL_EXACT && o.local_solver != GBP_LOCAL_FISTA) return GBP_ERR_INVALID_ARG;
+    if (o.local_solver == GBP_LOCAL_FISTA && (o.n_f < 1 || o.n_f > 256)) return GBP_ERR_INVALID_ARG;
+    if (!(o.eps >= 0.f) || !std::isfinite(o.eps)) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaSuccess;
+    if (o.local_solver == GBP_LOCAL_FISTA && !c->lip_valid) {
+        gbp::time_begin(c, 5);
+        e = gbp::launch_lipschitz(c);
+        gbp::time_end(c, 5);
+        if (e) return from_cuda(e);
+        c->lip_valid = true;
+    }
+    // keep a NOT_SPD latched by the precompute: the solve resets the control block
+    e = gbp::launch_fim(c, &o);
+    if (!e) e = gbp::launch_parent_pass(c, o.local_solver, o.n_f, phi, parent, alpha);
+    if (e) return from_cuda(e);
+    c->last_mode = o.local_solver;
+    c->last_nf = o.n_f;
+    c->solve_gen = c->param_gen;
+    return GBP_OK;
+}
+
+gbp_status gbp_get_solve_stats(gbp_ctx *c, gbp_solve_stats *s)
+{
+    if (!c || !s) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    gbp_status st = latched(c);
+    if (st == GBP_ERR_CUDA || st == GBP_ERR_NO_MEMORY) return st;
+    const Control &h = *c->h_ctl;
+    s->iterations = h.iterations;
+    s->candidates = (int64_t)h.candidates;
+    s->face_updates = (int64_t)h.face_updates;
+    s->fp64_fallbacks = (int64_t)h.fp64_fallbacks;
+    s->unreached = (int64_t)h.unreached;
+    s->adj_levels = h.adj_levels;
+    s->adj_cycle_nodes = h.adj_cycle_nodes;
+    s->adj_cycle_iters = h.adj_cycle_iters;
+    s->status = h.status ? h.status : h.param_status;
+    s->reserved = 0;
+    return (gbp_status)s->status;
+}
+
+gbp_status gbp_ecg_forward(gbp_ctx *c, const float *phi, const gbp_template *tmpl, int32_t precision, float *ecg)
+{
+    if (!c || !phi || !ecg || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
+    if (precision != GBP_PREC_FP32 && precision != GBP_PREC_BF16) return GBP_ERR_INVALID_ARG;
+    if (!c->N) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    return from_cuda(gbp::launch_ecg_forward(c, phi, tmpl, precision, ecg));
+}
+
+gbp_status gbp_ecg_loss_backward(gbp_ctx *c, const float *phi, const float *ecg, const float *target,
+                                 const gbp_template *tmpl, float *loss, float *dphi)
+{
+    if (!c || !phi || !ecg || !target || !loss || !dphi || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
+    if (!c->N) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    return from_cuda(gbp::launch_ecg_backward(c, phi, ecg, target, tmpl, loss, dphi));
+}
+
+gbp_status gbp_geodesic_backward(gbp_ctx *c, const float *dphi, float *d_cf, float *d_ct, float *d_t, float *d_x)
+{
+    if (!c || !dphi) return GBP_ERR_INVALID_ARG;
+    if (c->solve_gen < 0 || c->solve_gen != c->param_gen) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    return from_cuda(gbp::launch_adjoint(c, dphi, d_cf, d_ct, d_t, d_x));
+}
+
+gbp_status gbp_forward_backward(gbp_ctx *c, const gbp_solve_opts *opts, const gbp_template *tmpl,
+                                int32_t precision, const float *cf, const float *ct, const float *t,
+                                const float *target, float *loss, float *ecg, float *d_cf, float *d_ct,
+                                float *d_t, float *d_x)
+{
+    if (!c || !cf || !ct || !target || !loss || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v || !c->has_fib || !c->K || !c->N) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    gbp_status st = gbp_set_velocities(c, cf, ct);
+    if (st) return st;
+    if (t) {
+        cudaError_t e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * c->K, cudaMemcpyDeviceToDevice, c->stream);
+        if (e) return from_cuda(e);
+        c->param_gen++;
+    }
+    st = gbp_eikonal_solve(c, opts, nullptr, nullptr, nullptr);
+    if (st) return st;
+    int64_t NT = (int64_t)c->N * tmpl->T;
+    float *V = ecg;
+    if (!V) {
+        if (NT > c->ecg_tmp_cap) {
+            cudaError_t e = dalloc(&c->ecg_tmp, NT);
+            if (e) return from_cuda(e);
+            c->ecg_tmp_cap = NT;
+        }
+        V = c->ecg_tmp;
+    }
+    st = gbp_ecg_forward(c, c->phi, tmpl, precision, V);
+    if (st) return st;
+    st = gbp_ecg_loss_backward(c, c->phi, V, target, tmpl, loss, c->dphi);
+    if (st) return st;
+    return gbp_geodesic_backward(c, c->dphi, d_cf, d_ct, d_t, d_x);
+}
+
+gbp_status gbp_forward_backward_host(gbp_ctx *c, const gbp_solve_opts *opts, const gbp_template *tmpl,
+                                     int32_t precision, const float *cf, const float *ct, const float *t,
+                                     const float *target, float *loss, float *d_cf, float *d_ct, float *d_t,
+                                     float *d_x)
+{
+    if (!c || !cf || !ct || !target || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v || !c->has_fib || !c->K || !c->N) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    const int64_t n_t = c->n_t, K = c->K, NT = (int64_t)c->N * tmpl->T;
+    // staging layout: in = [cf | ct | t | target], out = [loss | d_cf | d_ct | d_t | d_x]
+    const int64_t in_n = 2 * n_t + K + NT, out_n = 1 + 2 * n_t + 4 * K;
+    cudaError_t e = cudaSuccess;
+    if (in_n > c->stage_in_cap) {
+        if (c->pin_in) cudaFreeHost(c->pin_in);
+        c->pin_in = nullptr;
+        e = dalloc(&c->dev_in, in_n);
+        if (!e) e = cudaMallocHost(&c->pin_in, sizeof(float) * in_n);
+        if (e) return from_cuda(e);
+        c->stage_in_cap = in_n;
+    }
+    if (out_n > c->stage_out_cap) {
+        if (c->pin_out) cudaFreeHost(c->pin_out);
+        c->pin_out = nullptr;
+        e = dalloc(&c->dev_out, out_n);
+        if (!e) e = cudaMallocHost(&c->pin_out, sizeof(float) * out_n);
+        if (e) return from_cuda(e);
+        c->stage_out_cap = out_n;
+    }
+    float *pi = c->pin_in, *po = c->pin_out, *di = c->dev_in, *dout = c->dev_out;
+    std::memcpy(pi, cf, sizeof(float) * n_t);
+    std::memcpy(pi + n_t, ct, sizeof(float) * n_t);
+    if (t) std::memcpy(pi + 2 * n_t, t, sizeof(float) * K);
+    std::memcpy(pi + 2 * n_t + K, target, sizeof(float) * NT);
+    e = cudaMemcpyAsync(di, pi, sizeof(float) * in_n, cudaMemcpyHostToDevice, c->stream);
+    if (e) return from_cuda(e);
+    gbp_status st = gbp_forward_backward(c, opts, tmpl, precision, di, di + n_t, t ? di + 2 * n_t : nullptr,
+                                         di + 2 * n_t + K, dout, nullptr, dout + 1, dout + 1 + n_t,
+                                         dout + 1 + 2 * n_t, dout + 1 + 2 * n_t + K);
+    if (st) return st;
+    e = cudaMemcpyAsync(po, dout, sizeof(float) * out_n, cudaMemcpyDeviceToHost, c->stream);
+    if (e) return from_cuda(e);
+    st = latched(c);
+    if (st) return st;
+    if (loss) *loss = po[0];
+    if (d_cf) std::memcpy(d_cf, po + 1, sizeof(float) * n_t);
+    if (d_ct) std::memcpy(d_ct, po + 1 + n_t, sizeof(float) * n_t);
+    if (d_t) std::memcpy(d_t, po + 1 + 2 * n_t, sizeof(float) * K);
+    if (d_x) std::memcpy(d_x, po + 1 + 2 * n_t + K, sizeof(float) * 3 * K);
+    return GBP_OK;
+}
+
+gbp_status gbp_local_solve_batch(gbp_ctx *c, int64_t n, const float *e, const float *fib, const float *cf,
+                                 const float *ct, const float *Phi, int32_t mode, int32_t n_f, float *value,
+                                 float *alpha)
+{
+    if (!c || n < 1 || !e || !fib || !cf || !ct || !Phi || !value || !alpha) return GBP_ERR_INVALID_ARG;
+    if (mode != GBP_LOCAL_EXACT && mode != GBP_LOCAL_FISTA) return GBP_ERR_INVALID_ARG;
+    if (mode == GBP_LOCAL_FISTA && (n_f < 1 || n_f > 256)) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaError_t err = cudaMemsetAsync(c->ctl, 0, offsetof(Control, param_status), c->stream);
+    if (!err) err = gbp::launch_local_batch(c, n, e, fib, cf, ct, Phi, mode, n_f, value, alpha);
+    return from_cuda(err);
+}
+
+gbp_status gbp_enable_timing(gbp_ctx *c, int32_t on)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (!on) gbp::flush_timing(c);
+    c->timing = on != 0;
+    return GBP_OK;
+}
+
+gbp_status gbp_get_kernel_times(gbp_ctx *c, int32_t n_classes, double *ms, int64_t *launches)
+{
+    if (!c || n_classes < 1 || n_classes > 8) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    gbp::flush_timing(c);
+    for (int i = 0; i < n_classes; ++i) {
+        if (ms) ms[i] = c->ms[i];
+        if (launches) launches[i] = c->cls_launches[i];
+    }
+    return GBP_OK;
+}
+
+gbp_status gbp_reset_kernel_times(gbp_ctx *c)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    gbp::flush_timing(c);
+    for (int i = 0; i < 8; ++i) {
+        c->ms[i] = 0.0;
+        c->cls_launches[i] = 0;
+    }
+    return GBP_OK;
+}
+
+int64_t gbp_launch_count(gbp_ctx *c) { return c ? c->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,507 @@
+// fim.cu -- eikonal solve: per-tet metric precompute, onset seeding, the
+// persistent active-list Fast Iterative Method (Algorithm 2 with the local
+// solver of Sec. II-B) and the parent pass.
+#include "gbp_internal.cuh"
+
+namespace gbp {
+
+// ---------------------------------------------------------------------------
+// per-tet metric (Sec. II-A): R = D^{1/2} in factored form
+// ---------------------------------------------------------------------------
+__global__ void k_precompute(int64_t n_t, const float *__restrict__ fib, const float *__restrict__ cf,
+                             const float *__restrict__ ct, float4 *__restrict__ tm, float *__restrict__ tsd,
+                             Control *ctl)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    float fx = fib[3 * j], fy = fib[3 * j + 1], fz = fib[3 * j + 2];
+    float nn = sqrtf(fx * fx + fy * fy + fz * fz);
+    float vf = cf[j], vt = ct[j];
+    bool bad = !(nn > 0.f) || !(vf > 0.f) || !(vt > 0.f) || !isfinite(vf) || !isfinite(vt) || !isfinite(nn);
+    if (bad) {
+        atomicCAS(&ctl->param_status, 0, (int)GBP_ERR_NOT_SPD);
+        nn = 1.f; fx = 1.f; fy = fz = 0.f;
+        vf = vt = 1.f;
+    }
+    float in = 1.f / nn;
+    float sa = 1.f / vt;
+    tm[j] = make_float4(fx * in, fy * in, fz * in, sa);
+    tsd[j] = 1.f / vf - sa;
+}
+
+cudaError_t launch_precompute(gbp_ctx *c)
+{
+    int th = 256;
+    int64_t bl = (c->n_t + th - 1) / th;
+    k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, c->fib, c->cf, c->ct, c->tm, c->tsd, c->ctl);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// transformed edge vectors of face (tet j, opposite slot s) seen from v_i
+__device__ __forceinline__ void face_vectors(const float4 *__restrict__ xyz, int4 tv, int s, float4 m, float sd,
+                                             float3 p[3], int fv[3])
+{
+    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+    int vi = ids[s];
+    float4 xi = __ldg(&xyz[vi]);
+    int a = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (q == s) continue;
+        fv[a] = ids[q];
+        float4 xq = __ldg(&xyz[ids[q]]);
+        p[a] = xform(make_float3(xq.x - xi.x, xq.y - xi.y, xq.z - xi.z), m, sd);
+        ++a;
+    }
+}
+
+__global__ void k_lipschitz(int64_t n_t, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
+                            const float4 *__restrict__ tm, const float *__restrict__ tsd, float4 *__restrict__ tlip)
+{
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n_t) return;
+    int4 tv = tets[j];
+    float4 m = tm[j];
+    float sd = tsd[j];
+    float L[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+        float3 p[3];
+        int fv[3];
+        face_vectors(xyz, tv, s, m, sd, p, fv);
+        L[s] = face_lipschitz(p);
+    }
+    tlip[j] = make_float4(L[0], L[1], L[2], L[3]);
+}
+
+cudaError_t launch_lipschitz(gbp_ctx *c)
+{
+    int th = 256;
+    int64_t bl = (c->n_t + th - 1) / th;
+    k_lipschitz<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, c->xyz, c->tets, c->tm, c->tsd, c->tlip);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// onset seeding (Algorithm 2 initialisation, Eq. upwind_xi)
+// ---------------------------------------------------------------------------
+// Order-preserving map of a float onto an unsigned key, so that the smallest
+// value (ties: smallest onset index) wins an atomicMin.
+__device__ __forceinline__ unsigned int float_key(float v)
+{
+    unsigned int b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned int k)
+{
+    unsigned int b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
+__global__ void k_onset_keys(int K, int kind, const int *__restrict__ idx, const float *__restrict__ bary,
+                             const float *__restrict__ t, int64_t n_v, int64_t n_t, const float4 *__restrict__ xyz,
+                             const int4 *__restrict__ tets, const float4 *__restrict__ tm,
+                             const float *__restrict__ tsd, unsigned long long *keys, Control *ctl)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    int id = idx[k];
+    if (kind == GBP_ONSET_NODAL) {
+        if (id < 0 || id >= n_v) {
+            atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
+            return;
+        }
+        unsigned long long key = ((unsigned long long)float_key(t[k]) << 32) | (unsigned)k;
+        atomicMin(&keys[id], key);
+    } else {
+        if (id < 0 || id >= n_t) {
+            atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
+            return;
+        }
+        int4 tv = tets[id];
+        int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+        float4 x[4];
+        float3 xo = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x[q] = xyz[ids[q]];
+            float b = bary[4 * k + q];
+            xo.x = fmaf(b, x[q].x, xo.x);
+            xo.y = fmaf(b, x[q].y, xo.y);
+            xo.z = fmaf(b, x[q].z, xo.z);
+        }
+        float4 m = tm[id];
+        float sd = tsd[id];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float3 w = xform(make_float3(x[q].x - xo.x, x[q].y - xo.y, x[q].z - xo.z), m, sd);
+            float v = t[k] + sqrtf(f3dot(w, w));
+            unsigned long long key = ((unsigned long long)float_key(v) << 32) | (unsigned)k;
+            atomicMin(&keys[ids[q]], key);
+        }
+    }
+}
+
+// Per vertex: decode the onset key, reset the FIM state.
+__global__ void k_init_nodes(int64_t n_v, const unsigned long long *__restrict__ keys, float *phi, int4 *rec,
+                             int *chg, int *stamp)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_v) return;
+    unsigned long long key = keys[i];
+    if (key != ~0ull) {
+        phi[i] = key_float((unsigned int)(key >> 32));
+        rec[i] = make_int4(-1 - (int)(key & 0xffffffffu), 0, 0, 0);
+        chg[i] = 0;
+    } else {
+        phi[i] = GBP_INF;
+        rec[i] = make_int4(GBP_UNREACHED, 0, 0, 0);
+        chg[i] = -1000000;
+    }
+    stamp[i] = 0;
+}
+
+// Seeded vertices put their neighbours on the first active list.
+__global__ void k_seed_lists(int64_t n_v, const unsigned long long *__restrict__ keys, const int *__restrict__ n2n_ptr,
+                             const int *__restrict__ n2n, int *stamp, int *list1, Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_v || keys[i] == ~0ull) return;
+    for (int e = n2n_ptr[i]; e < n2n_ptr[i + 1]; ++e) {
+        int m = n2n[e];
+        if (atomicMax(&stamp[m], 1) < 1) {
+            int pos = atomicAdd(&ctl->count[1], 1);
+            list1[pos] = m;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// persistent FIM (Algorithm 2)
+// ---------------------------------------------------------------------------
+struct FimArgs {
+    int64_t n_v;
+    const float4 *xyz;
+    const int4 *tets;
+    const float4 *tm;
+    const float *tsd;
+    const float4 *tlip;
+    const int *n2t_ptr, *n2t, *n2n_ptr, *n2n;
+    float *phi;
+    int4 *rec;
+    int *chg, *stamp, *lists;
+    Control *ctl;
+    float eps;
+    int max_iters;
+    int n_f;
+};
+
+// One iteration k = one Jacobi-style sweep of Algorithm 2 restricted to the
+// active vertices (neighbours of the vertices that changed at k-1), run
+// warp-cooperatively: the warp owns one vertex i, its lanes take i's
+// incident tets from the vertex->tet adjacency, solve the local problem of
+// every face E_{j\i} that has a vertex changed since k-1 (the optional mask
+// of Algorithm 2) and reduce the minimum (Eq. hopflax_global).  A vertex
+// that decreased by more than eps is marked changed and activates its
+// neighbours for k+1.  Reads of neighbour values may see this iteration's
+// updates (chaotic relaxation); the operator is monotone so the limit is the
+// same fixed point.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_fim(FimArgs a)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp_in_block = threadIdx.x >> 5;
+    const int warps_per_block = blockDim.x >> 5;
+    const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + warp_in_block;
+    const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+    const int64_t n_v = a.n_v;
+    __shared__ unsigned long long s_cand, s_faces;
+    __shared__ int s_fb;
+    if (threadIdx.x == 0) {
+        s_cand = 0;
+        s_faces = 0;
+        s_fb = 0;
+    }
+    __syncthreads();
+    unsigned int nbar = 0;
+    int k = 1;
+    int fb_local = 0;
+    for (; k <= a.max_iters; ++k) {
+        const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
+        const int n_cand = ld_relaxed_i32(&a.ctl->count[cur]);
+        if (n_cand == 0) break;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->count[nn] = 0;
+        const int *list = a.lists + (int64_t)cur * n_v;
+        int *nlist = a.lists + (int64_t)nxt * n_v;
+        unsigned int my_faces = 0;
+        for (int64_t w = gwarp; w < n_cand; w += nwarps) {
+            const int i = __ldcg(&list[w]);
+            const float phi_old = __ldcg(&a.phi[i]);
+            const int beg = __ldg(&a.n2t_ptr[i]), end = __ldg(&a.n2t_ptr[i + 1]);
+            float best = GBP_INF;
+            int best_code = 0x7fffffff;
+            for (int e0 = beg; e0 < end; e0 += 32) {
+                const int e = e0 + lane;
+                float v = GBP_INF;
+                int code = 0x7fffffff;
+                if (e < end) {
+                    code = __ldg(&a.n2t[e]);
+                    const int j = code >> 2, s = code & 3;
+                    const int4 tv = __ldg(&a.tets[j]);
+                    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+                    bool need = false;
+                    float ph[3];
+                    int q3 = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (q == s) continue;
+                        need |= __ldcg(&a.chg[ids[q]]) >= k - 1;
+                        ph[q3++] = __ldcg(&a.phi[ids[q]]);
+                    }
+                    if (need) {
+                        ++my_faces;
+                        float3 p[3];
+                        int fv[3];
+                        face_vectors(a.xyz, tv, s, __ldg(&a.tm[j]), __ldg(&a.tsd[j]), p, fv);
+                        LocalRes r;
+                        if (MODE == GBP_LOCAL_FISTA) {
+                            float4 Lq = __ldg(&a.tlip[j]);
+                            float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
+                            r = local_fista(p, ph, Lv, a.n_f);
+                        } else {
+                            r = local_exact(p, ph, &fb_local);
+                        }
+                        v = r.v;
+                    }
+                }
+                // lexicographic (value, code) minimum over the warp
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    float ov = __shfl_xor_sync(0xffffffffu, v, off);
+                    int oc = __shfl_xor_sync(0xffffffffu, code, off);
+                    if (ov < v || (ov == v && oc < code)) {
+                        v = ov;
+                        code = oc;
+                    }
+                }
+                if (v < best || (v == best && code < best_code)) {
+                    best = v;
+                    best_code = code;
+                }
+            }
+            bool changed = false;
+            if (best < phi_old) {
+                changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
+                if (lane == 0) {
+                    a.phi[i] = best;
+                    a.rec[i].x = best_code;
+                    if (changed) a.chg[i] = k;
+                }
+            }
+            if (changed) {
+                // activate the neighbours of i for iteration k+1
+                const int nb = __ldg(&a.n2n_ptr[i]), ne = __ldg(&a.n2n_ptr[i + 1]);
+                for (int e0 = nb; e0 < ne; e0 += 32) {
+                    const int e = e0 + lane;
+                    bool app = false;
+                    int m = 0;
+                    if (e < ne) {
+                        m = __ldg(&a.n2n[e]);
+                        app = atomicMax(&a.stamp[m], k + 1) < k + 1;
+                    }
+                    warp_append(app, m, nlist, &a.ctl->count[nxt]);
+                }
+            }
+        }
+        // statistics
+        unsigned int wf = my_faces;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) wf += __shfl_xor_sync(0xffffffffu, wf, off);
+        if (lane == 0 && wf) atomicAdd(&s_faces, (unsigned long long)wf);
+        if (gwarp == 0 && lane == 0) atomicAdd(&s_cand, (unsigned long long)n_cand);
+        ++nbar;
+        if (!grid_barrier(a.ctl, nbar * gridDim.x)) break;
+    }
+    if (fb_local) atomicAdd(&s_fb, fb_local);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_cand) atomicAdd(&a.ctl->candidates, s_cand);
+        if (s_faces) atomicAdd(&a.ctl->face_updates, s_faces);
+        if (s_fb) atomicAdd(&a.ctl->fp64_fallbacks, (unsigned long long)s_fb);
+        if (blockIdx.x == 0) {
+            a.ctl->iterations = k - 1;
+            if (k > a.max_iters && !ld_relaxed_i32(&a.ctl->abort))
+                atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_NOT_CONVERGED);
+        }
+    }
+}
+
+static int fim_grid(gbp_ctx *c, const void *fn)
+{
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 8) per_sm = 8;
+    return per_sm * c->num_sms;
+}
+
+cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
+{
+    cudaError_t err;
+    const int64_t n_v = c->n_v;
+    // reset the control block (counters, status) and the onset keys; the
+    // precompute's status word (last field) is kept
+    err = cudaMemsetAsync(c->ctl, 0, offsetof(Control, param_status), c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(c->keys, 0xff, sizeof(unsigned long long) * n_v, c->stream);
+    if (err) return err;
+    int th = 256;
+    k_onset_keys<<<(c->K + th - 1) / th, th, 0, c->stream>>>(c->K, c->onset_kind, c->on_idx, c->on_bary, c->on_t,
+                                                              n_v, c->n_t, c->xyz, c->tets, c->tm, c->tsd, c->keys,
+                                                              c->ctl);
+    unsigned bl = (unsigned)((n_v + th - 1) / th);
+    k_init_nodes<<<bl, th, 0, c->stream>>>(n_v, c->keys, c->phi, c->rec, c->chg, c->stamp);
+    k_seed_lists<<<bl, th, 0, c->stream>>>(n_v, c->keys, c->n2n_ptr, c->n2n, c->stamp, c->lists + n_v, c->ctl);
+    c->launches += 3;
+    if ((err = cudaGetLastError())) return err;
+
+    FimArgs a;
+    a.n_v = n_v;
+    a.xyz = c->xyz;
+    a.tets = c->tets;
+    a.tm = c->tm;
+    a.tsd = c->tsd;
+    a.tlip = c->tlip;
+    a.n2t_ptr = c->n2t_ptr;
+    a.n2t = c->n2t;
+    a.n2n_ptr = c->n2n_ptr;
+    a.n2n = c->n2n;
+    a.phi = c->phi;
+    a.rec = c->rec;
+    a.chg = c->chg;
+    a.stamp = c->stamp;
+    a.lists = c->lists;
+    a.ctl = c->ctl;
+    a.eps = o->eps;
+    a.max_iters = o->max_iters;
+    a.n_f = o->n_f;
+    const void *fn = o->local_solver == GBP_LOCAL_FISTA ? (const void *)k_fim<GBP_LOCAL_FISTA>
+                                                        : (const void *)k_fim<GBP_LOCAL_EXACT>;
+    int grid = fim_grid(c, fn);
+    void *args[] = {&a};
+    time_begin(c, 0);
+    err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, c->stream);
+    time_end(c, 0);
+    c->launches++;
+    return err;
+}
+
+// ---------------------------------------------------------------------------
+// parent pass: alpha of the final parent face with the final values
+// ---------------------------------------------------------------------------
+template <int MODE>
+__global__ void k_parent_pass(int64_t n_v, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
+                              const float4 *__restrict__ tm, const float *__restrict__ tsd,
+                              const float4 *__restrict__ tlip, int n_f, const float *__restrict__ phi, int4 *rec,
+                              float *out_phi, int32_t *out_parent, float *out_alpha, Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_v) return;
+    int4 r = rec[i];
+    int code = r.x;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    float pv = phi[i];
+    if (code >= 0) {
+        int j = code >> 2, s = code & 3;
+        int4 tv = tets[j];
+        float3 p[3];
+        int fv[3];
+        face_vectors(xyz, tv, s, tm[j], tsd[j], p, fv);
+        float ph[3] = {phi[fv[0]], phi[fv[1]], phi[fv[2]]};
+        LocalRes lr;
+        int fb = 0;
+        if (MODE == GBP_LOCAL_FISTA) {
+            float4 Lq = tlip[j];
+            float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
+            lr = local_fista(p, ph, Lv, n_f);
+        } else {
+            lr = local_exact(p, ph, &fb);
+        }
+        a0 = lr.a0;
+        a1 = lr.a1;
+        a2 = lr.a2;
+        rec[i] = make_int4(code, __float_as_int(a0), __float_as_int(a1), __float_as_int(a2));
+    } else if (code == GBP_UNREACHED) {
+        atomicAdd(&ctl->unreached, 1ull);
+    }
+    if (out_phi) out_phi[i] = pv;
+    if (out_parent) out_parent[i] = code;
+    if (out_alpha) {
+        out_alpha[3 * i] = a0;
+        out_alpha[3 * i + 1] = a1;
+        out_alpha[3 * i + 2] = a2;
+    }
+}
+
+cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_t *parent, float *alpha)
+{
+    int th = 256;
+    unsigned bl = (unsigned)((c->n_v + th - 1) / th);
+    time_begin(c, 1);
+    if (mode == GBP_LOCAL_FISTA)
+        k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>(c->n_v, c->xyz, c->tets, c->tm, c->tsd, c->tlip,
+                                                                 n_f, c->phi, c->rec, phi, parent, alpha, c->ctl);
+    else
+        k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>(c->n_v, c->xyz, c->tets, c->tm, c->tsd, c->tlip,
+                                                                 n_f, c->phi, c->rec, phi, parent, alpha, c->ctl);
+    time_end(c, 1);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// local problems on independent faces (diagnostic entry point)
+// ---------------------------------------------------------------------------
+__global__ void k_local_batch(int64_t n, const float *__restrict__ e, const float *__restrict__ fib,
+                              const float *__restrict__ cf, const float *__restrict__ ct,
+                              const float *__restrict__ Phi, int mode, int n_f, float *value, float *alpha,
+                              Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float fx = fib[3 * i], fy = fib[3 * i + 1], fz = fib[3 * i + 2];
+    float in = rsqrtf(fx * fx + fy * fy + fz * fz);
+    float sa = 1.f / ct[i];
+    float4 m = make_float4(fx * in, fy * in, fz * in, sa);
+    float sd = 1.f / cf[i] - sa;
+    float3 p[3];
+    float ph[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        p[a] = xform(make_float3(e[9 * i + 3 * a], e[9 * i + 3 * a + 1], e[9 * i + 3 * a + 2]), m, sd);
+        ph[a] = Phi[3 * i + a];
+    }
+    LocalRes r;
+    int fb = 0;
+    if (mode == GBP_LOCAL_FISTA) r = local_fista(p, ph, face_lipschitz(p), n_f);
+    else r = local_exact(p, ph, &fb);
+    if (fb) atomicAdd(&ctl->fp64_fallbacks, (unsigned long long)fb);
+    value[i] = r.v;
+    alpha[3 * i] = r.a0;
+    alpha[3 * i + 1] = r.a1;
+    alpha[3 * i + 2] = r.a2;
+}
+
+cudaError_t launch_local_batch(gbp_ctx *c, int64_t n, const float *e, const float *fib, const float *cf,
+                               const float *ct, const float *Phi, int mode, int n_f, float *value, float *alpha)
+{
+    int th = 128;
+    unsigned bl = (unsigned)((n + th - 1) / th);
+    k_local_batch<<<bl, th, 0, c->stream>>>(n, e, fib, cf, ct, Phi, mode, n_f, value, alpha, c->ctl);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+}  // namespace gbp

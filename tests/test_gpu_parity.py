@@ -1,0 +1,265 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
+same seeded inputs.  Tolerances: phi within 1e-4 relative, parents bit-exact
+where the oracle's argmin is unambiguous (margin > 1e-5 phi), ECG within 1e-3
+relative L2, gradients within 1e-3 relative L2."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O  # noqa: E402
+from paper_2308_08410_gb300 import gbp  # noqa: E402
+from paper_2308_08410_gb300 import synth as S  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = gbp.Context(0)
+    yield c
+    c.close()
+
+
+def dev(a, dtype=np.float32):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype)).cuda()
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def jittered_c1(n=20, seed=0, kind="element", K=3):
+    p = S.make_c1(n=n, seed=seed)
+    r = np.random.default_rng(seed + 1234)
+    p.cf = (p.cf * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+    p.ct = (p.ct * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+    if kind == "element":
+        p.onsets = S.onsets_element(p.mesh, K, seed=seed + 7, tmin=0.0, tmax=6.0)
+    ek = O.eikonal(p.mesh, p.fib, (p.cf * 1.07).astype(np.float32), p.ct, p.onsets)
+    p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, seed + 5)
+    return p
+
+
+def check_eikonal(ctx, p, opts=None, rtol=1e-4, mode=O.EXACT, n_f=32):
+    gbp.setup_problem(ctx, p)
+    phi, parent, alpha = ctx.eikonal_solve(opts)
+    st = ctx.stats()
+    assert st["status"] == 0, st
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, mode=mode, n_f=n_f)
+    g = phi.cpu().numpy().astype(float)
+    fin = np.isfinite(ref["phi"])
+    np.testing.assert_array_equal(np.isfinite(g), fin)
+    rel = np.abs(g[fin] - ref["phi"][fin]) / np.maximum(1.0, np.abs(ref["phi"][fin]))
+    assert rel.max() < rtol, (rel.max(), st)
+    return g, parent.cpu().numpy(), alpha.cpu().numpy(), ref, st
+
+
+# ---------------------------------------------------------------------------
+# local solver
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("skinny", [False, True])
+def test_local_exact(ctx, skinny):
+    e, f, cf, ct, phi = S.random_faces(20000, seed=3 + skinny, skinny=skinny)
+    v_ref, a_ref = O.local_batch(e, f, cf, ct, phi)
+    v, a = ctx.local_solve_batch(dev(e), dev(f), dev(cf), dev(ct), dev(phi))
+    v = v.cpu().numpy().astype(float)
+    rel = np.abs(v - v_ref) / np.maximum(1.0, np.abs(v_ref))
+    assert rel.max() < 2e-6, rel.max()
+    # minimiser agrees where the problem is well conditioned
+    a = a.cpu().numpy()
+    assert np.median(np.abs(a - a_ref).max(axis=1)) < 1e-4
+
+
+def test_local_fista(ctx):
+    e, f, cf, ct, phi = S.random_faces(20000, seed=5, p_inf=0.15)
+    v_ref, _ = O.local_batch(e, f, cf, ct, phi, mode=O.FISTA, n_f=32)
+    v, _ = ctx.local_solve_batch(dev(e), dev(f), dev(cf), dev(ct), dev(phi), mode=gbp.LOCAL_FISTA, n_f=32)
+    v = v.cpu().numpy().astype(float)
+    rel = np.abs(v - v_ref) / np.maximum(1.0, np.abs(v_ref))
+    assert np.quantile(rel, 0.999) < 1e-5 and rel.max() < 1e-3, (np.quantile(rel, 0.999), rel.max())
+
+
+# ---------------------------------------------------------------------------
+# eikonal
+# ---------------------------------------------------------------------------
+
+def test_eikonal_c1(ctx):
+    p = S.make_c1()
+    g, par, al, ref, st = check_eikonal(ctx, p)
+    unamb = ref["margin"] > 1e-5 * np.maximum(1.0, ref["phi"])
+    assert unamb.mean() > 0.9
+    np.testing.assert_array_equal(par[unamb], ref["parent"][unamb])
+    assert st["iterations"] > 5 and st["face_updates"] > p.mesh.n_v
+
+
+def test_eikonal_ragged_sizes(ctx):
+    """Meshes that leave partial warps / tiles: 7^3 and 13 x 13 x 13 cubes with
+    element onsets, and a single tet."""
+    for n in (7, 13):
+        p = jittered_c1(n=n, seed=n)
+        check_eikonal(ctx, p)
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32)
+    tets = np.array([[0, 1, 2, 3]], np.int32)
+    mesh = S.Mesh(xyz, tets)
+    p = S.Problem("one", mesh, np.array([[1, 0, 0]], np.float32), np.array([0.6], np.float32),
+                  np.array([0.3], np.float32),
+                  S.Onsets(S.ONSET_NODAL, np.array([0], np.int32), np.array([2.0], np.float32)),
+                  np.ones((1, 4), np.float32), S.Template(T=8))
+    check_eikonal(ctx, p)
+
+
+def test_eikonal_biv(ctx):
+    p = S.make_c2()
+    g, par, al, ref, st = check_eikonal(ctx, p)
+    unamb = ref["margin"] > 1e-5 * np.maximum(1.0, ref["phi"])
+    assert np.mean(par[unamb] == ref["parent"][unamb]) > 0.999
+
+
+def test_eikonal_eps_and_unreached(ctx):
+    a = S.kuhn_cube(6, 1.0)
+    xyz = np.concatenate([a.xyz, a.xyz + np.float32(3.0)])
+    tets = np.concatenate([a.tets, a.tets + a.n_v]).astype(np.int32)
+    mesh = S.Mesh(xyz, tets)
+    n_t = mesh.n_t
+    p = S.Problem("two", mesh, np.tile(np.array([[0.6, 0.8, 0]], np.float32), (n_t, 1)),
+                  np.full(n_t, 0.6, np.float32), np.full(n_t, 0.3, np.float32),
+                  S.Onsets(S.ONSET_NODAL, np.array([3], np.int32), np.array([1.0], np.float32)),
+                  np.ones((1, mesh.n_v), np.float32), S.Template(T=8))
+    g, par, al, ref, st = check_eikonal(ctx, p, opts=gbp.make_opts(eps=1e-5))
+    assert st["unreached"] == a.n_v
+    assert np.all(par[a.n_v:] == gbp.UNREACHED)
+
+
+def test_eikonal_fista_mode(ctx):
+    """Algorithm 1 face values are upper bounds; the FISTA-mode solution lies
+    between the exact fixed point and the exact one plus the FISTA error."""
+    p = S.make_c1(n=14)
+    gbp.setup_problem(ctx, p)
+    phi, _, _ = ctx.eikonal_solve(gbp.make_opts(local_solver=gbp.LOCAL_FISTA, n_f=48))
+    assert ctx.stats()["status"] == 0
+    ex = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)["phi"]
+    rel = (phi.cpu().numpy() - ex) / np.maximum(1, ex)
+    assert rel.min() > -2e-6 and rel.max() < 1e-2
+
+
+# ---------------------------------------------------------------------------
+# ECG and misfit (same phi on both sides: the oracle's, rounded to float32)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("T", [150, 37, 500])
+def test_ecg_forward_fp32(ctx, T):
+    p = S.make_c1(T=T)
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    phi32 = ref["phi"].astype(np.float32)
+    gbp.setup_problem(ctx, p)
+    V = ctx.ecg_forward(dev(phi32), p.tmpl).cpu().numpy()
+    Vr = O.ecg(p.L, phi32.astype(float), p.tmpl)
+    assert rel_l2(V, Vr) < 1e-3, rel_l2(V, Vr)
+    assert rel_l2(V, Vr) < 1e-5  # what FP32 actually achieves here
+
+
+def test_ecg_loss_backward(ctx):
+    p = jittered_c1()
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    phi32 = ref["phi"].astype(np.float32)
+    gbp.setup_problem(ctx, p)
+    V = ctx.ecg_forward(dev(phi32), p.tmpl)
+    loss, dphi = ctx.ecg_loss_backward(dev(phi32), V, dev(p.extra["target"]), p.tmpl)
+    Vr = O.ecg(p.L, phi32.astype(float), p.tmpl)
+    lr, lam = O.loss_grad_phi(p.L, phi32.astype(float), p.tmpl, Vr, p.extra["target"])
+    assert abs(loss.item() - lr) / lr < 1e-4
+    assert rel_l2(dphi.cpu().numpy(), lam) < 1e-3, rel_l2(dphi.cpu().numpy(), lam)
+
+
+# ---------------------------------------------------------------------------
+# gradients
+# ---------------------------------------------------------------------------
+
+def gradient_case(ctx, p, precision=gbp.PREC_FP32):
+    dp = gbp.setup_problem(ctx, p)
+    out = ctx.forward_backward(dp.cf, dp.ct, dev(p.extra["target"]), p.tmpl, precision=precision)
+    st = ctx.stats()
+    assert st["status"] == 0, st
+    ref = O.forward_backward(p.mesh, p.fib, p.cf, p.ct, p.onsets, p.L, p.tmpl, p.extra["target"])
+    return {k: v.cpu().numpy() for k, v in out.items()}, ref, st
+
+
+@pytest.mark.parametrize("kind", ["element", "nodal"])
+def test_gradient_generic(ctx, kind):
+    p = jittered_c1(kind=kind)
+    g, ref, st = gradient_case(ctx, p)
+    assert abs(g["loss"][0] - ref["loss"]) / ref["loss"] < 1e-4
+    for k in ("d_cf", "d_ct", "d_t"):
+        assert rel_l2(g[k], ref[k]) < 1e-3, (k, rel_l2(g[k], ref[k]), st)
+    if kind == "element":
+        assert rel_l2(g["d_x"], ref["d_x"]) < 1e-3
+    else:
+        assert np.all(g["d_x"] == 0)
+
+
+def test_gradient_c1_plain(ctx):
+    """Plain c1: tets of one depth share a metric, so edge/vertex minimisers
+    tie between tets and the per-tet velocity gradient is not unique there.
+    The onset-time gradient (through mu only) is unique; velocity gradients
+    are compared along smooth directions, which are insensitive to which of
+    the tied neighbouring tets receives the contribution."""
+    p = S.make_c1()
+    ek = O.eikonal(p.mesh, p.fib, (p.cf * 1.07).astype(np.float32), p.ct, p.onsets)
+    p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 5)
+    g, ref, st = gradient_case(ctx, p)
+    assert rel_l2(g["d_t"], ref["d_t"]) < 1e-3
+    cen = p.mesh.xyz.astype(float)[p.mesh.tets].mean(axis=1)
+    for k in range(4):
+        d = np.cos(0.3 * (k + 1) * cen[:, 0] + 0.2 * k * cen[:, 1]) + 0.1 * cen[:, 2]
+        for name in ("d_cf", "d_ct"):
+            a, b = float(g[name] @ d), float(ref[name] @ d)
+            assert abs(a - b) <= 2e-3 * abs(b) + 1e-3 * np.abs(ref[name]).sum() * 1e-3, (name, a, b)
+
+
+def test_gradient_biv_cycles(ctx):
+    """BiV mesh: the parent graph holds cycles; the adjoint must resolve them."""
+    p = S.make_c2(h=1.6)
+    r = np.random.default_rng(3)
+    p.cf = (p.cf * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+    ek = O.eikonal(p.mesh, p.fib, (p.cf * 1.05).astype(np.float32), p.ct, p.onsets)
+    p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 9)
+    g, ref, st = gradient_case(ctx, p)
+    for k in ("d_cf", "d_ct", "d_t", "d_x"):
+        assert rel_l2(g[k], ref[k]) < 1e-3, (k, rel_l2(g[k], ref[k]), st)
+
+
+def test_host_entry_point_matches_device(ctx):
+    p = jittered_c1(n=12)
+    dp = gbp.setup_problem(ctx, p)
+    tgt = dev(p.extra["target"])
+    out = ctx.forward_backward(dp.cf, dp.ct, tgt, p.tmpl)
+    d = {k: v.cpu().numpy() for k, v in out.items()}
+    h = ctx.forward_backward_host(p.cf, p.ct, p.extra["target"], p.tmpl)
+    assert abs(h["loss"][0] - d["loss"][0]) <= 1e-6 * abs(d["loss"][0])
+    for k in ("d_cf", "d_ct", "d_t", "d_x"):
+        assert rel_l2(h[k], d[k]) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# error handling (host validation, latched device status)
+# ---------------------------------------------------------------------------
+
+def test_errors(ctx):
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 1]], np.float32)
+    bad = np.array([[0, 2, 1, 3]], np.int32)  # inverted
+    with pytest.raises(gbp.GbpError) as ei:
+        ctx.upload_mesh(xyz, bad)
+    assert ei.value.status == 2
+    with pytest.raises(gbp.GbpError):
+        ctx.upload_mesh(xyz, np.array([[0, 1, 2, 9]], np.int32))
+    ctx.upload_mesh(xyz, np.array([[0, 1, 2, 3]], np.int32))
+    ctx.set_fibres(dev([[1, 0, 0]]))
+    ctx.set_velocities(dev([-0.5]), dev([0.3]))
+    st = ctx.stats()
+    assert st["status_code"] == 3
+    with pytest.raises(gbp.GbpError) as ei:
+        ctx.geodesic_backward(dev(np.zeros(5)))
+    assert ei.value.status == 8
