@@ -276,8 +276,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             a.xj[i] = xn;
             a.acc[i] = 0.f;
         }
-        // converged when no entry moved by more than 1e-7 of its own size
-        float crit = dmax - 1e-7f * xmax;
+        // converged when no entry moved by more than 2e-6 of the largest |x|:
+        // FP32 atomic accumulation in varying order jitters sums by an ulp
+        // (~1.2e-7 relative), so a tighter test could never be met
+        float crit = dmax - 2e-6f * xmax;
         if (crit > 0.f) atomicMax((int *)&a.ctl->adj_delta[it & 1], __float_as_int(crit));
         ++nbar;
         if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
