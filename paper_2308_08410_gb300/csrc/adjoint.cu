@@ -34,7 +34,7 @@ struct AdjArgs {
     int onset_kind;
     const int *on_idx;
     const float *on_bary;
-    float *mu, *xj, *acc;
+    float *mu, *xj, *acc, *acc2;
     int *cnt, *proc, *lists;
     float *d_cf, *d_ct, *d_t, *d_x;
     Control *ctl;
@@ -235,6 +235,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         if (app) {
             a.xj[i] = ld_cg_f(&a.mu[i]);
             a.acc[i] = 0.f;
+            a.acc2[i] = 0.f;
         }
         warp_append(app, (int)i, R, &a.ctl->count[3]);
     }
@@ -242,48 +243,66 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
     const int nR = ld_relaxed_i32(&a.ctl->count[3]);
     if (nR == 0) return;
-    // x <- base + P_R^T x, base = mu (lam + pushes of processed children)
+    // x <- base + P_R^T x with base = mu (lam plus the pushes of processed
+    // children).  One barrier per iteration: the update of x reads the sums
+    // pushed in the previous iteration (buffer cur) and pushes the new x into
+    // the other buffer.  Stop when max |dx| <= 2e-6 max |x| over all of R
+    // (FP32 sums in varying atomic order jitter by about an ulp).
+    float *acc_cur = a.acc, *acc_nxt = a.acc2;
+    auto push = [&](int i, float x, float *dst) {
+        const int4 r = __ldg(&a.rec[i]);
+        if (r.x < 0) return;
+        const int j = r.x >> 2, s = r.x & 3;
+        const int4 tv = __ldg(&a.tets[j]);
+        const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
+        const int f0 = s == 0 ? tv.y : tv.x;
+        const int f1 = s <= 1 ? tv.z : tv.y;
+        const int f2 = s <= 2 ? tv.w : tv.z;
+        if (al[0] != 0.f) atomicAdd(&dst[f0], al[0] * x);
+        if (al[1] != 0.f) atomicAdd(&dst[f1], al[1] * x);
+        if (al[2] != 0.f) atomicAdd(&dst[f2], al[2] * x);
+    };
+    for (int64_t w = tid; w < nR; w += nth) {
+        const int i = __ldcg(&R[w]);
+        push(i, ld_cg_f(&a.xj[i]), acc_cur);
+    }
+    ++nbar;
+    if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
     int it = 0;
     for (; it < a.max_cycle_iters; ++it) {
-        for (int64_t w = tid; w < nR; w += nth) {
-            const int i = __ldcg(&R[w]);
-            const int4 r = __ldg(&a.rec[i]);
-            if (r.x < 0) continue;
-            const float x = ld_cg_f(&a.xj[i]);
-            const int j = r.x >> 2, s = r.x & 3;
-            const int4 tv = __ldg(&a.tets[j]);
-            int ids[4] = {tv.x, tv.y, tv.z, tv.w};
-            const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-            int q3 = 0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                if (q == s) continue;
-                if (al[q3] != 0.f) atomicAdd(&a.acc[ids[q]], al[q3] * x);
-                ++q3;
-            }
+        // slot (it+1)%3 was last read before the previous barrier
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.ctl->adj_delta[(it + 1) % 3] = 0.f;
+            a.ctl->adj_xmax[(it + 1) % 3] = 0.f;
         }
-        ++nbar;
-        if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
-        // slot (it+1)&1 was last read before this iteration's first barrier
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->adj_delta[(it + 1) & 1] = 0.f;
         float dmax = 0.f, xmax = 0.f;
         for (int64_t w = tid; w < nR; w += nth) {
             const int i = __ldcg(&R[w]);
-            const float xn = ld_cg_f(&a.mu[i]) + ld_cg_f(&a.acc[i]);
+            const float xn = ld_cg_f(&a.mu[i]) + ld_cg_f(&acc_cur[i]);
             const float xo = ld_cg_f(&a.xj[i]);
+            acc_cur[i] = 0.f;
             dmax = fmaxf(dmax, fabsf(xn - xo));
             xmax = fmaxf(xmax, fabsf(xn));
             a.xj[i] = xn;
-            a.acc[i] = 0.f;
+            push(i, xn, acc_nxt);
         }
-        // converged when no entry moved by more than 2e-6 of the largest |x|:
-        // FP32 atomic accumulation in varying order jitters sums by an ulp
-        // (~1.2e-7 relative), so a tighter test could never be met
-        float crit = dmax - 2e-6f * xmax;
-        if (crit > 0.f) atomicMax((int *)&a.ctl->adj_delta[it & 1], __float_as_int(crit));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+            xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (dmax > 0.f) atomicMax((int *)&a.ctl->adj_delta[it % 3], __float_as_int(dmax));
+            if (xmax > 0.f) atomicMax((int *)&a.ctl->adj_xmax[it % 3], __float_as_int(xmax));
+        }
         ++nbar;
         if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
-        if (__int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_delta[it & 1])) <= 0.f) {
+        const float gd = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_delta[it % 3]));
+        const float gx = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_xmax[it % 3]));
+        float *t = acc_cur;
+        acc_cur = acc_nxt;
+        acc_nxt = t;
+        if (gd <= 2e-6f * gx) {
             ++it;
             break;
         }
@@ -311,7 +330,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->barrier, 0, sizeof(unsigned int) * 2, c->stream);  // barrier, abort
     if (err) return err;
-    err = cudaMemsetAsync(&c->ctl->adj_levels, 0, sizeof(int) * 4 + 2 * sizeof(float), c->stream);
+    err = cudaMemsetAsync(&c->ctl->adj_levels, 0, sizeof(int) * 4 + 6 * sizeof(float), c->stream);
     if (err) return err;
     if (d_cf) cudaMemsetAsync(d_cf, 0, sizeof(float) * c->n_t, c->stream);
     if (d_ct) cudaMemsetAsync(d_ct, 0, sizeof(float) * c->n_t, c->stream);
@@ -340,6 +359,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.mu = c->mu;
     a.xj = c->jac_x;
     a.acc = c->jac_acc;
+    a.acc2 = c->jac_acc2;
     a.cnt = c->cnt;
     a.proc = c->proc;
     a.lists = c->lists;

@@ -73,6 +73,7 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->mu);
     dfree(&c->jac_x);
     dfree(&c->jac_acc);
+    dfree(&c->jac_acc2);
     dfree(&c->cnt);
     dfree(&c->proc);
     dfree(&c->L);
@@ -329,6 +330,7 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     CK(dalloc(&c->mu, n_v));
     CK(dalloc(&c->jac_x, n_v));
     CK(dalloc(&c->jac_acc, n_v));
+    CK(dalloc(&c->jac_acc2, n_v));
     CK(dalloc(&c->cnt, n_v));
     CK(dalloc(&c->proc, n_v));
     CK(dalloc(&c->dphi, n_v));

@@ -38,22 +38,29 @@ cudaError_t launch_precompute(gbp_ctx *c)
     return cudaGetLastError();
 }
 
-// transformed edge vectors of face (tet j, opposite slot s) seen from v_i
+// vertices of the face of tet tv opposite slot s, in increasing slot order
+__device__ __forceinline__ void face_ids(int4 tv, int s, int &vi, int &f0, int &f1, int &f2)
+{
+    vi = s == 0 ? tv.x : s == 1 ? tv.y : s == 2 ? tv.z : tv.w;
+    f0 = s == 0 ? tv.y : tv.x;
+    f1 = s <= 1 ? tv.z : tv.y;
+    f2 = s <= 2 ? tv.w : tv.z;
+}
+
+// transformed edge vectors p_n = R (v_{j_n} - v_i) of face (tet tv, opposite slot s)
 __device__ __forceinline__ void face_vectors(const float4 *__restrict__ xyz, int4 tv, int s, float4 m, float sd,
                                              float3 p[3], int fv[3])
 {
-    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
-    int vi = ids[s];
-    float4 xi = __ldg(&xyz[vi]);
-    int a = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (q == s) continue;
-        fv[a] = ids[q];
-        float4 xq = __ldg(&xyz[ids[q]]);
-        p[a] = xform(make_float3(xq.x - xi.x, xq.y - xi.y, xq.z - xi.z), m, sd);
-        ++a;
-    }
+    int vi, f0, f1, f2;
+    face_ids(tv, s, vi, f0, f1, f2);
+    fv[0] = f0;
+    fv[1] = f1;
+    fv[2] = f2;
+    const float4 xi = __ldg(&xyz[vi]);
+    const float4 x0 = __ldg(&xyz[f0]), x1 = __ldg(&xyz[f1]), x2 = __ldg(&xyz[f2]);
+    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
+    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
+    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
 }
 
 __global__ void k_lipschitz(int64_t n_t, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
@@ -199,27 +206,35 @@ struct FimArgs {
 };
 
 // One iteration k = one Jacobi-style sweep of Algorithm 2 restricted to the
-// active vertices (neighbours of the vertices that changed at k-1), run
-// warp-cooperatively: the warp owns one vertex i, its lanes take i's
-// incident tets from the vertex->tet adjacency, solve the local problem of
-// every face E_{j\i} that has a vertex changed since k-1 (the optional mask
-// of Algorithm 2) and reduce the minimum (Eq. hopflax_global).  A vertex
-// that decreased by more than eps is marked changed and activates its
-// neighbours for k+1.  Reads of neighbour values may see this iteration's
-// updates (chaotic relaxation); the operator is monotone so the limit is the
-// same fixed point.
+// active vertices (neighbours of the vertices that changed at k-1).  A group
+// of FIM_G lanes owns one active vertex i: its lanes take i's incident tets
+// from the vertex->tet adjacency, solve the local problem of every face
+// E_{j\i} that has a vertex changed since k-1 (the optional mask of
+// Algorithm 2) and reduce the minimum (Eq. hopflax_global).  A vertex that
+// decreased by more than eps is marked changed and activates its neighbours
+// for k+1 (appended through a per-CTA shared-memory buffer, one global
+// atomic per CTA and iteration).  Reads of neighbour values may see this
+// iteration's updates (chaotic relaxation); the operator is monotone, so the
+// limit is the same fixed point.
+constexpr int FIM_G = 8;       // lanes per active vertex
+constexpr int FIM_CAP = 2048;  // per-CTA append buffer (overflow goes straight to global)
+
 template <int MODE>
-__global__ void __launch_bounds__(256) k_fim(FimArgs a)
+__global__ void __launch_bounds__(256, 4) k_fim(FimArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const int warp_in_block = threadIdx.x >> 5;
-    const int warps_per_block = blockDim.x >> 5;
-    const int64_t gwarp = (int64_t)blockIdx.x * warps_per_block + warp_in_block;
-    const int64_t nwarps = (int64_t)gridDim.x * warps_per_block;
+    const int sub = lane & (FIM_G - 1);
+    const int gl = lane & ~(FIM_G - 1);  // first lane of this group
+    const int groups_per_block = blockDim.x / FIM_G;
+    const int64_t ggroup = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / FIM_G;
+    const int64_t ngroups = (int64_t)gridDim.x * groups_per_block;
     const int64_t n_v = a.n_v;
+    __shared__ int s_list[FIM_CAP];
+    __shared__ int s_n, s_cnt, s_base;
     __shared__ unsigned long long s_cand, s_faces;
     __shared__ int s_fb;
     if (threadIdx.x == 0) {
+        s_n = 0;
         s_cand = 0;
         s_faces = 0;
         s_fb = 0;
@@ -228,103 +243,127 @@ __global__ void __launch_bounds__(256) k_fim(FimArgs a)
     unsigned int nbar = 0;
     int k = 1;
     int fb_local = 0;
+    unsigned int my_faces = 0;
     for (; k <= a.max_iters; ++k) {
         const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
         const int n_cand = ld_relaxed_i32(&a.ctl->count[cur]);
         if (n_cand == 0) break;
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->count[nn] = 0;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.ctl->count[nn] = 0;
+            s_cand += (unsigned long long)n_cand;
+        }
         const int *list = a.lists + (int64_t)cur * n_v;
         int *nlist = a.lists + (int64_t)nxt * n_v;
-        unsigned int my_faces = 0;
-        for (int64_t w = gwarp; w < n_cand; w += nwarps) {
-            const int i = __ldcg(&list[w]);
-            const float phi_old = __ldcg(&a.phi[i]);
-            const int beg = __ldg(&a.n2t_ptr[i]), end = __ldg(&a.n2t_ptr[i + 1]);
+        for (int64_t g = ggroup;; g += ngroups) {
+            const bool act = g < n_cand;
+            if (!__any_sync(0xffffffffu, act)) break;
+            int i = 0, beg = 0, end = 0;
+            float phi_old = 0.f;
+            if (act) {
+                i = __ldcg(&list[g]);
+                phi_old = __ldcg(&a.phi[i]);
+                beg = __ldg(&a.n2t_ptr[i]);
+                end = __ldg(&a.n2t_ptr[i + 1]);
+            }
+            const int maxdeg = __reduce_max_sync(0xffffffffu, end - beg);
             float best = GBP_INF;
             int best_code = 0x7fffffff;
-            for (int e0 = beg; e0 < end; e0 += 32) {
-                const int e = e0 + lane;
-                float v = GBP_INF;
-                int code = 0x7fffffff;
+            for (int e0 = 0; e0 < maxdeg; e0 += FIM_G) {
+                const int e = beg + e0 + sub;
                 if (e < end) {
-                    code = __ldg(&a.n2t[e]);
+                    const int code = __ldg(&a.n2t[e]);
                     const int j = code >> 2, s = code & 3;
                     const int4 tv = __ldg(&a.tets[j]);
-                    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
-                    bool need = false;
-                    float ph[3];
-                    int q3 = 0;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (q == s) continue;
-                        need |= __ldcg(&a.chg[ids[q]]) >= k - 1;
-                        ph[q3++] = __ldcg(&a.phi[ids[q]]);
-                    }
-                    if (need) {
+                    int vi, f0, f1, f2;
+                    face_ids(tv, s, vi, f0, f1, f2);
+                    const int c0 = __ldcg(&a.chg[f0]), c1 = __ldcg(&a.chg[f1]), c2 = __ldcg(&a.chg[f2]);
+                    const float ph[3] = {__ldcg(&a.phi[f0]), __ldcg(&a.phi[f1]), __ldcg(&a.phi[f2])};
+                    if (max(c0, max(c1, c2)) >= k - 1) {
                         ++my_faces;
                         float3 p[3];
                         int fv[3];
                         face_vectors(a.xyz, tv, s, __ldg(&a.tm[j]), __ldg(&a.tsd[j]), p, fv);
                         LocalRes r;
                         if (MODE == GBP_LOCAL_FISTA) {
-                            float4 Lq = __ldg(&a.tlip[j]);
-                            float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
+                            const float4 Lq = __ldg(&a.tlip[j]);
+                            const float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
                             r = local_fista(p, ph, Lv, a.n_f);
                         } else {
                             r = local_exact(p, ph, &fb_local);
                         }
-                        v = r.v;
+                        if (r.v < best || (r.v == best && code < best_code)) {
+                            best = r.v;
+                            best_code = code;
+                        }
                     }
                 }
-                // lexicographic (value, code) minimum over the warp
+            }
+            // lexicographic (value, code) minimum over the group
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    float ov = __shfl_xor_sync(0xffffffffu, v, off);
-                    int oc = __shfl_xor_sync(0xffffffffu, code, off);
-                    if (ov < v || (ov == v && oc < code)) {
-                        v = ov;
-                        code = oc;
-                    }
-                }
-                if (v < best || (v == best && code < best_code)) {
-                    best = v;
-                    best_code = code;
+            for (int off = FIM_G / 2; off > 0; off >>= 1) {
+                const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+                const int oc = __shfl_xor_sync(0xffffffffu, best_code, off);
+                if (ov < best || (ov == best && oc < best_code)) {
+                    best = ov;
+                    best_code = oc;
                 }
             }
             bool changed = false;
-            if (best < phi_old) {
+            if (act && best < phi_old) {
                 changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
-                if (lane == 0) {
+                if (sub == 0) {
                     a.phi[i] = best;
                     a.rec[i].x = best_code;
                     if (changed) a.chg[i] = k;
                 }
             }
+            // activate the neighbours of changed vertices for iteration k+1
+            int nb = 0, ne = 0;
             if (changed) {
-                // activate the neighbours of i for iteration k+1
-                const int nb = __ldg(&a.n2n_ptr[i]), ne = __ldg(&a.n2n_ptr[i + 1]);
-                for (int e0 = nb; e0 < ne; e0 += 32) {
-                    const int e = e0 + lane;
-                    bool app = false;
-                    int m = 0;
-                    if (e < ne) {
-                        m = __ldg(&a.n2n[e]);
-                        app = atomicMax(&a.stamp[m], k + 1) < k + 1;
+                nb = __ldg(&a.n2n_ptr[i]);
+                ne = __ldg(&a.n2n_ptr[i + 1]);
+            }
+            const int maxn = __reduce_max_sync(0xffffffffu, ne - nb);
+            for (int e0 = 0; e0 < maxn; e0 += FIM_G) {
+                const int e = nb + e0 + sub;
+                if (e < ne) {
+                    const int m = __ldg(&a.n2n[e]);
+                    if (atomicMax(&a.stamp[m], k + 1) < k + 1) {
+                        const int pos = atomicAdd(&s_n, 1);
+                        if (pos < FIM_CAP) {
+                            s_list[pos] = m;
+                        } else {
+                            nlist[atomicAdd(&a.ctl->count[nxt], 1)] = m;
+                        }
                     }
-                    warp_append(app, m, nlist, &a.ctl->count[nxt]);
                 }
             }
+            (void)gl;
         }
-        // statistics
-        unsigned int wf = my_faces;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) wf += __shfl_xor_sync(0xffffffffu, wf, off);
-        if (lane == 0 && wf) atomicAdd(&s_faces, (unsigned long long)wf);
-        if (gwarp == 0 && lane == 0) atomicAdd(&s_cand, (unsigned long long)n_cand);
+        // flush the CTA's appends with one global reservation
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int n = min(s_n, FIM_CAP);
+            s_cnt = n;
+            s_base = n ? atomicAdd(&a.ctl->count[nxt], n) : 0;
+            s_n = 0;
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < s_cnt; q += blockDim.x) nlist[s_base + q] = s_list[q];
         ++nbar;
         if (!grid_barrier(a.ctl, nbar * gridDim.x)) break;
     }
-    if (fb_local) atomicAdd(&s_fb, fb_local);
+    // statistics
+    unsigned int wf = my_faces;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wf += __shfl_xor_sync(0xffffffffu, wf, off);
+    int wfb = fb_local;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) wfb += __shfl_xor_sync(0xffffffffu, wfb, off);
+    if (lane == 0) {
+        if (wf) atomicAdd(&s_faces, (unsigned long long)wf);
+        if (wfb) atomicAdd(&s_fb, wfb);
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         if (s_cand) atomicAdd(&a.ctl->candidates, s_cand);
@@ -343,7 +382,6 @@ static int fim_grid(gbp_ctx *c, const void *fn)
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
     if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
     return per_sm * c->num_sms;
 }
 

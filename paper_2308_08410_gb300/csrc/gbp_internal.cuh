@@ -31,8 +31,9 @@ struct Control {
     int adj_cycle_nodes;
     int adj_cycle_iters;
     int adj_processed;
-    float adj_delta[2];           // convergence measure of the cycle iteration (double-buffered)
-    int pad;
+    float adj_delta[3];           // max |dx| of the cycle iteration (rotating slots)
+    float adj_xmax[3];            // max |x| of the cycle iteration (rotating slots)
+    int pad[3];
     int param_status;             // latched by the metric precompute (kept across solves)
 };
 
@@ -96,22 +97,25 @@ __device__ __forceinline__ float eval_alpha(const float3 p[3], const float ph[3]
 
 // Interior stationary point of the face (all three values finite), FP64.
 // Same algebra as the FP32 branch below; used when the FP32 discriminant
-// or the face is too close to degenerate.
-static __device__ __noinline__ bool interior_fp64(const float3 p[3], const float ph[3], float *b0o, float *b1o)
+// or the face is too close to degenerate.  Scalar arguments keep the caller's
+// operands in registers.
+static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0z, float p1x, float p1y, float p1z,
+                                                  float p2x, float p2y, float p2z, float ph0, float ph1, float ph2,
+                                                  float *b0o, float *b1o)
 {
-    double d1x = (double)p[0].x - p[2].x, d1y = (double)p[0].y - p[2].y, d1z = (double)p[0].z - p[2].z;
-    double d2x = (double)p[1].x - p[2].x, d2y = (double)p[1].y - p[2].y, d2z = (double)p[1].z - p[2].z;
+    double d1x = (double)p0x - p2x, d1y = (double)p0y - p2y, d1z = (double)p0z - p2z;
+    double d2x = (double)p1x - p2x, d2y = (double)p1y - p2y, d2z = (double)p1z - p2z;
     double Q00 = d1x * d1x + d1y * d1y + d1z * d1z;
     double Q01 = d1x * d2x + d1y * d2y + d1z * d2z;
     double Q11 = d2x * d2x + d2y * d2y + d2z * d2z;
     double nx = d1y * d2z - d1z * d2y, ny = d1z * d2x - d1x * d2z, nz = d1x * d2y - d1y * d2x;
     double det = nx * nx + ny * ny + nz * nz;
     if (!(det > 0.0)) return false;
-    double q0 = d1x * p[2].x + d1y * p[2].y + d1z * p[2].z;
-    double q1 = d2x * p[2].x + d2y * p[2].y + d2z * p[2].z;
-    double D0 = (double)ph[0] - ph[2], D1 = (double)ph[1] - ph[2];
+    double q0 = d1x * p2x + d1y * p2y + d1z * p2z;
+    double q1 = d2x * p2x + d2y * p2y + d2z * p2z;
+    double D0 = (double)ph0 - ph2, D1 = (double)ph1 - ph2;
     double k = (Q11 * D0 * D0 - 2.0 * Q01 * D0 * D1 + Q00 * D1 * D1) / det;
-    double tp = nx * p[2].x + ny * p[2].y + nz * p[2].z;
+    double tp = nx * p2x + ny * p2y + nz * p2z;
     double S = tp * tp / det;
     if (!(k < 1.0) || !(S > 0.0)) return false;
     double h = sqrt(S / (1.0 - k));
@@ -183,7 +187,8 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
             bool found = false;
             if (degenerate || 1.f - k < 1e-3f) {
                 ++*fb;
-                found = interior_fp64(p, ph, &b0, &b1);
+                found = interior_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, ph[0],
+                                      ph[1], ph[2], &b0, &b1);
             } else {
                 float h = sqrtf(S / (1.f - k));
                 float y0 = fmaf(h, D0, q0), y1 = fmaf(h, D1, q1);
@@ -418,7 +423,7 @@ struct gbp_ctx {
     int last_mode = 0, last_nf = 0;
     int64_t param_gen = 0, solve_gen = -1;
     // adjoint state
-    float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr;
+    float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;
     int *cnt = nullptr, *proc = nullptr;
     // ECG scratch
     float *ecg_part = nullptr;

@@ -223,7 +223,9 @@ def test_gradient_biv_cycles(ctx):
     """BiV mesh: the parent graph holds cycles; the adjoint must resolve them."""
     p = S.make_c2(h=1.6)
     r = np.random.default_rng(3)
+    # jitter both velocities: the isotropic fast layer otherwise ties exactly
     p.cf = (p.cf * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+    p.ct = (p.ct * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
     ek = O.eikonal(p.mesh, p.fib, (p.cf * 1.05).astype(np.float32), p.ct, p.onsets)
     p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 9)
     g, ref, st = gradient_case(ctx, p)
@@ -263,3 +265,42 @@ def test_errors(ctx):
     with pytest.raises(gbp.GbpError) as ei:
         ctx.geodesic_backward(dev(np.zeros(5)))
     assert ei.value.status == 8
+
+
+# ---------------------------------------------------------------------------
+# BF16 tensor-core ECG
+# ---------------------------------------------------------------------------
+
+def _bf16_round(x):
+    """Round float32 to the nearest BF16 (ties to even), returned as float64."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("T", [150, 300, 500])
+def test_ecg_forward_bf16(ctx, T):
+    """Tensor-core path: against an emulation of its quantisation (BF16
+    sigma and per-lead-scaled BF16 lead field, FP32 row sums) it agrees to
+    FP32 accumulation error, and against the FP64 oracle it stays within the
+    BF16 error budget (reported per workload in the benchmark)."""
+    p = S.make_c1(T=T)
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    phi32 = ref["phi"].astype(np.float32)
+    gbp.setup_problem(ctx, p)
+    V = ctx.ecg_forward(dev(phi32), p.tmpl, precision=gbp.PREC_BF16).cpu().numpy()
+    assert ctx.stats()["status"] == 0
+    Vr = O.ecg(p.L, phi32.astype(float), p.tmpl)
+    # emulation of the quantised contraction
+    tm = p.tmpl
+    ts = tm.t0 + tm.dt * np.arange(tm.T)
+    z = 4.0 * (ts[None, :] - phi32.astype(np.float64)[:, None]) / tm.tau
+    sig = _bf16_round((1.0 / (1.0 + np.exp(-z))).astype(np.float32))
+    L = p.L.astype(np.float32)
+    scale = np.abs(L).max(axis=1).astype(np.float32)
+    Lq = _bf16_round((L / scale[:, None]).astype(np.float32))
+    rows = L.astype(np.float64).sum(axis=1)
+    Ve = tm.K0 * rows[:, None] + (tm.K1 - tm.K0) * scale[:, None].astype(np.float64) * (Lq @ sig)
+    assert rel_l2(V, Ve) < 1e-3, rel_l2(V, Ve)
+    err = rel_l2(V, Vr)
+    assert err < 5e-2, err
