@@ -215,6 +215,32 @@ gbp_status gbp_forward_backward_host(gbp_ctx *ctx, const gbp_solve_opts *opts,
                                      float *d_ct, float *d_t, float *d_x);
 
 /* ------------------------------------------------------------------ */
+/* allocation-free entry point                                          */
+/* ------------------------------------------------------------------ */
+
+/* The ECG forward pass of gbp_ecg_forward (FP32) for callers that must not
+ * allocate device memory: code under a fixed memory budget, code inside a
+ * framework whose caching allocator owns the device heap, and loops that must
+ * never block on cudaMalloc / cudaFree.  It needs no context and calls no
+ * allocating routine.  (The paper has no counterpart: this is a deployment
+ * variant of the ECG contraction.)
+ *
+ * L device float32 [N][n_v] (1 <= N <= 16), phi device float32 [n_v],
+ * ecg device float32 [N][T] (written), T <= 4096, stream a cudaStream_t or
+ * NULL.  Runs on the calling thread's current CUDA device.
+ * Scratch: a 4 MiB file-scope device array (partial sums and row sums) that
+ * every GPU loading the library holds until the process exits.  The first
+ * call on a device looks up that array's address (once per device); make
+ * that first call before any stream capture.  All calls share the array and
+ * every call overwrites what it reads, so nothing carries over between
+ * calls; calls that overlap on the GPU (other streams, other threads) race
+ * on it and must be serialised by the caller.
+ * Errors: GBP_ERR_INVALID_ARG for a NULL pointer or N, T beyond the limits
+ * above; GBP_ERR_CUDA for a CUDA runtime error. */
+gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t n_v, const float *phi,
+                                   const gbp_template *tmpl, float *ecg, void *stream);
+
+/* ------------------------------------------------------------------ */
 /* diagnostics                                                          */
 /* ------------------------------------------------------------------ */
 

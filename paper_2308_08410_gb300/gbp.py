@@ -93,6 +93,7 @@ def load():
         "gbp_get_kernel_times": ([P, i32, P, P], i32),
         "gbp_reset_kernel_times": ([P], i32),
         "gbp_launch_count": ([P], i64),
+        "gbp_ecg_forward_noalloc": ([P, i32, i64, P, C.POINTER(Template), P, P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -111,6 +112,7 @@ def exported_symbols():
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
         "gbp_forward_backward_host", "gbp_local_solve_batch", "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
+        "gbp_ecg_forward_noalloc",
     ]
 
 
