@@ -215,6 +215,56 @@ gbp_status gbp_forward_backward_host(gbp_ctx *ctx, const gbp_solve_opts *opts,
                                      float *d_ct, float *d_t, float *d_x);
 
 /* ------------------------------------------------------------------ */
+/* learned initialiser: network training and inference kernels          */
+/* ------------------------------------------------------------------ */
+/* A 1-D convolutional network + MLP maps an ECG to initial onset sites,
+ * times and velocities, then Geodesic-BP refines them (not in the paper:
+ * the initialiser of the inverse problem of Sec. II-D).  All calls are
+ * stream-ordered on the context stream and take device pointers.  BF16
+ * operands are raw 16-bit storage (void*).  Activations are channels-last
+ * f32 [batch][length][channels]; convolution weights [C_out][ksize][C_in].
+ * GEMM operands keep the reduction dimension contiguous, zero-padded to a
+ * multiple of 64 (Kp). */
+
+/* C[m][n] = alpha sum_k A[m][k] B[n][k] + beta C[m][n]: A bf16 [M][lda],
+ * B bf16 [N][ldb] (k < Kp, Kp % 64 == 0, lda, ldb >= Kp and % 8 == 0),
+ * C f32 [M][ldc].  Tensor cores (tcgen05, FP32 accumulation in TMEM). */
+gbp_status gbp_nn_gemm_bf16(gbp_ctx *ctx, int32_t M, int32_t N, int32_t Kp, const void *A, int32_t lda,
+                            const void *B, int32_t ldb, float *C, int32_t ldc, float alpha, float beta);
+/* col[b*Lo + l][k*Ci + c] = act[b][stride*l + k - pad][c] (0 outside), bf16,
+ * row stride ldc >= ks*Ci (padding zeroed). */
+gbp_status gbp_nn_im2col(gbp_ctx *ctx, int32_t B, int32_t Li, int32_t Ci, int32_t Lo, int32_t ks,
+                         int32_t stride, int32_t pad, const float *act, void *col, int32_t ldc);
+/* the transpose colT[k*Ci + c][b*Lo + l], rows < Kp, row stride ldt >= B*Lo. */
+gbp_status gbp_nn_im2col_t(gbp_ctx *ctx, int32_t B, int32_t Li, int32_t Ci, int32_t Lo, int32_t ks,
+                           int32_t stride, int32_t pad, const float *act, int32_t Kp, void *colT,
+                           int32_t ldt);
+/* adjoint of im2col: dact[b][j][c] = sum of dcol entries that read act[b][j][c]. */
+gbp_status gbp_nn_col2im(gbp_ctx *ctx, int32_t B, int32_t Li, int32_t Ci, int32_t Lo, int32_t ks,
+                         int32_t stride, int32_t pad, const float *dcol, int32_t ldc, float *dact);
+/* y[m][n] = act(y[m][n] + bias[n]) in place (row stride ld), act = GELU
+ * (x Phi(x)) when gelu != 0; pre (may be NULL) keeps y + bias [M][N]. */
+gbp_status gbp_nn_bias_act(gbp_ctx *ctx, int32_t M, int32_t N, float *y, int32_t ld, const float *bias,
+                           float *pre, int32_t gelu);
+/* dy[m][n] *= GELU'(pre[m][n]) in place. */
+gbp_status gbp_nn_gelu_backward(gbp_ctx *ctx, int32_t M, int32_t N, float *dy, int32_t ld,
+                                const float *pre);
+/* db[n] = sum_m dz[m][n]. */
+gbp_status gbp_nn_bias_grad(gbp_ctx *ctx, int32_t M, int32_t N, const float *dz, int32_t ld, float *db);
+/* dst[r][c] = bf16(src[r][c]), zero for cols <= c < ldd. */
+gbp_status gbp_nn_cast_bf16(gbp_ctx *ctx, int32_t rows, int32_t cols, const float *src, int32_t lds,
+                            void *dst, int32_t ldd);
+/* dst[c][r] = bf16(src[r][c]) (dst has cols rows of stride ldd >= rows, zero padded). */
+gbp_status gbp_nn_transpose_bf16(gbp_ctx *ctx, int32_t rows, int32_t cols, const float *src, int32_t lds,
+                                 void *dst, int32_t ldd);
+/* loss = mean (y - t)^2 over n values (device scalar), dy = 2 (y - t) / n. */
+gbp_status gbp_nn_mse(gbp_ctx *ctx, int32_t n, const float *y, const float *t, float *dy, float *loss);
+/* Adam step `step` (>= 1) on FP32 master weights w with moments m1, m2;
+ * w_bf16 (may be NULL) receives the updated weights in BF16. */
+gbp_status gbp_nn_adam(gbp_ctx *ctx, int64_t n, float *w, const float *g, float *m1, float *m2, float lr,
+                       float beta1, float beta2, float eps, int32_t step, void *w_bf16);
+
+/* ------------------------------------------------------------------ */
 /* allocation-free entry point                                          */
 /* ------------------------------------------------------------------ */
 

@@ -14,11 +14,15 @@
 //
 // mu = (I - P^T)^{-1} dL/dphi is accumulated children-first: a vertex is
 // processed once every child (vertex whose parent face holds it with
-// alpha > 0) has pushed alpha * mu into it (topological levels, one grid
-// barrier per level).  The parent graph of the discrete fixed point can hold
-// short cycles (non-causal updates in anisotropic elements); the vertices
-// they block are finished by a bounded fixed-point (Jacobi) iteration on the
-// remaining sub-graph, which is closed under taking parents.
+// alpha > 0) has pushed alpha * mu into it.  This runs as a dataflow with no
+// grid barriers: the child whose decrement brings a parent's child count to
+// zero continues with that parent itself (further parents it readies go to a
+// work queue), so the critical path is the depth of the parent graph times
+// one vertex's latency.  The parent graph of the discrete fixed point can
+// hold short cycles (non-causal updates in anisotropic elements); the
+// vertices they block are finished by a bounded fixed-point (Jacobi)
+// iteration on the remaining sub-graph, which is closed under taking
+// parents.
 #include "gbp_internal.cuh"
 
 namespace gbp {
@@ -147,15 +151,38 @@ __global__ void k_adj_count(int64_t n_v, const int4 *__restrict__ rec, const int
     }
 }
 
-__global__ void k_adj_seed(int64_t n_v, const int *__restrict__ cnt, const int *__restrict__ proc, int *list1,
+// vertices with no children start the dataflow: they go to the work queue
+__global__ void k_adj_seed(int64_t n_v, const int *__restrict__ cnt, const int *__restrict__ proc, int *queue,
                            Control *ctl)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool app = i < n_v && proc[i] == 0 && cnt[i] == 0;
-    warp_append(app, (int)i, list1, &ctl->count[1]);
+    unsigned int mask = __ballot_sync(0xffffffffu, app);
+    if (mask == 0) return;
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) {
+        base = atomicAdd(&ctl->q_res, __popc(mask));
+        atomicAdd(&ctl->q_active, __popc(mask));
+        atomicAdd(&ctl->adj_levels, __popc(mask));  // number of seeds, reported in the stats
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (app) queue[base + __popc(mask & ((1u << lane) - 1u))] = (int)i;
 }
 
 __device__ __forceinline__ float ld_cg_f(const float *p) { return __ldcg(p); }
+
+__device__ __forceinline__ int ld_acquire_i32(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_i32(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
 {
@@ -166,69 +193,91 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     __shared__ int s_proc;
     if (threadIdx.x == 0) s_proc = 0;
     __syncthreads();
-    int levels = 0;
     bool ok = true;
-    // ---- topological levels ----
-    for (int k = 1;; ++k) {
-        const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
-        const int n_cur = ld_relaxed_i32(&a.ctl->count[cur]);
-        if (n_cur == 0) break;
-        ++levels;
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->count[nn] = 0;
-        const int *list = a.lists + (int64_t)cur * n_v;
-        int *nlist = a.lists + (int64_t)nxt * n_v;
-        int mine = 0;
-        for (int64_t base = 0; base < n_cur; base += nth) {
-            const int64_t w = base + tid;
-            bool app[3] = {false, false, false};
-            int vv[3] = {0, 0, 0};
-            if (w < n_cur) {
-                const int i = __ldcg(&list[w]);
-                const float m = ld_cg_f(&a.mu[i]);
-                const int4 r = __ldg(&a.rec[i]);
-                a.proc[i] = 1;
-                ++mine;
-                local_terms(a, i, r, m);
-                if (r.x >= 0) {
-                    const int j = r.x >> 2, s = r.x & 3;
-                    const int4 tv = __ldg(&a.tets[j]);
-                    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
-                    const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-                    int q3 = 0;
+    int mine = 0;
+    // ---- dataflow phase (no grid barrier per level) ----
+    // The vertices readied so far sit in a work queue (lists[0..n_v), slots
+    // start at -1).  Every thread takes tickets; the holder of ticket h
+    // processes the vertex in slot h, then continues itself with the first
+    // parent it readies (the child that brings a parent's count to zero) and
+    // queues any further ones.  q_active counts queued items plus chains in
+    // progress; it reaches zero only when no more work can appear.
+    int *queue = a.lists;
+    for (;;) {
+        const int h = atomicAdd(&a.ctl->q_head, 1);
+        int v = -1;
+        unsigned int spins = 0, sleep_ns = 32;
+        for (;;) {
+            if (h < n_v) {
+                v = ld_acquire_i32(&queue[h]);
+                if (v >= 0) break;
+            }
+            if ((spins & 15) == 0) {
+                if (ld_acquire_i32(&a.ctl->q_active) == 0) {
+                    // the last push (if any) happened before the count reached zero
+                    if (h < n_v) v = ld_acquire_i32(&queue[h]);
+                    break;
+                }
+                if (ld_relaxed_i32(&a.ctl->abort)) break;
+            }
+            if (++spins > (1u << 21)) {
+                atomicExch(&a.ctl->abort, 1);
+                atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 1024) sleep_ns <<= 1;
+        }
+        if (v < 0) break;
+        while (v >= 0) {
+            const float m = ld_cg_f(&a.mu[v]);
+            const int4 r = __ldg(&a.rec[v]);
+            a.proc[v] = 1;
+            ++mine;
+            local_terms(a, v, r, m);
+            int next = -1;
+            if (r.x >= 0) {
+                const int j = r.x >> 2, s = r.x & 3;
+                const int4 tv = __ldg(&a.tets[j]);
+                const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
+                const int f[3] = {s == 0 ? tv.y : tv.x, s <= 1 ? tv.z : tv.y, s <= 2 ? tv.w : tv.z};
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        if (q == s) continue;
-                        if (al[q3] != 0.f) {
-                            const int v = ids[q];
-                            atomicAdd(&a.mu[v], al[q3] * m);
-                            __threadfence();
-                            if (atomicSub(&a.cnt[v], 1) == 1) {
-                                app[q3] = true;
-                                vv[q3] = v;
-                            }
-                        }
-                        ++q3;
+                for (int q = 0; q < 3; ++q)
+                    if (al[q] != 0.f) atomicAdd(&a.mu[f[q]], al[q] * m);
+                // the pushes land before the counts they release
+                __threadfence();
+                int left[3] = {1, 1, 1};
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    if (al[q] != 0.f) left[q] = atomicSub(&a.cnt[f[q]], 1);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (al[q] == 0.f || left[q] != 1) continue;
+                    if (next < 0) {
+                        next = f[q];
+                    } else {
+                        atomicAdd(&a.ctl->q_active, 1);
+                        const int pos = atomicAdd(&a.ctl->q_res, 1);
+                        st_release_i32(&queue[pos], f[q]);
                     }
                 }
             }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) warp_append(app[q], vv[q], nlist, &a.ctl->count[nxt]);
+            v = next;
+            if (v >= 0) __threadfence();
         }
-        if (mine) atomicAdd(&s_proc, mine);
-        ++nbar;
-        if (!grid_barrier(a.ctl, nbar * gridDim.x)) {
-            ok = false;
-            break;
-        }
+        __threadfence();
+        atomicSub(&a.ctl->q_active, 1);
     }
+    if (mine) atomicAdd(&s_proc, mine);
     __syncthreads();
     if (threadIdx.x == 0 && s_proc) atomicAdd(&a.ctl->adj_processed, s_proc);
-    if (!ok) return;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->adj_levels = levels;
+    ++nbar;
+    if (!grid_barrier(a.ctl, nbar) || !ok) return;
     // ---- vertices blocked by cycles: fixed-point iteration ----
     // collect the unprocessed reached vertices R (closed under parents); the
-    // last level barrier ordered every write of the level loop before this
-    int *R = a.lists;  // no list is live any more
+    // barrier above ordered every write of the dataflow phase before this
+    int *R = a.lists + n_v;
     for (int64_t base = 0; base < n_v; base += nth) {
         const int64_t i = base + tid;
         bool app = i < n_v && __ldcg(&a.proc[i]) == 0;
@@ -240,7 +289,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         warp_append(app, (int)i, R, &a.ctl->count[3]);
     }
     ++nbar;
-    if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
+    if (!grid_barrier(a.ctl, nbar)) return;
     const int nR = ld_relaxed_i32(&a.ctl->count[3]);
     if (nR == 0) return;
     // x <- base + P_R^T x with base = mu (lam plus the pushes of processed
@@ -267,7 +316,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         push(i, ld_cg_f(&a.xj[i]), acc_cur);
     }
     ++nbar;
-    if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
+    if (!grid_barrier(a.ctl, nbar)) return;
     int it = 0;
     for (; it < a.max_cycle_iters; ++it) {
         // slot (it+1)%3 was last read before the previous barrier
@@ -296,7 +345,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             if (xmax > 0.f) atomicMax((int *)&a.ctl->adj_xmax[it % 3], __float_as_int(xmax));
         }
         ++nbar;
-        if (!grid_barrier(a.ctl, nbar * gridDim.x)) return;
+        if (!grid_barrier(a.ctl, nbar)) return;
         const float gd = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_delta[it % 3]));
         const float gx = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_xmax[it % 3]));
         float *t = acc_cur;
@@ -328,7 +377,17 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     // keep the solve's statistics, reset the adjoint counters
     err = cudaMemsetAsync(c->ctl->count, 0, sizeof(int) * 4, c->stream);
     if (err) return err;
-    err = cudaMemsetAsync(&c->ctl->barrier, 0, sizeof(unsigned int) * 2, c->stream);  // barrier, abort
+    err = cudaMemsetAsync(&c->ctl->barrier, 0, sizeof(unsigned int) * 2, c->stream);  // arrivals, abort
+    if (err) return err;
+    err = cudaMemsetAsync(&c->ctl->bar_gen, 0, sizeof(unsigned int), c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(&c->ctl->q_head, 0, sizeof(int), c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(&c->ctl->q_res, 0, sizeof(int), c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(&c->ctl->q_active, 0, sizeof(int), c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(c->lists, 0xff, sizeof(int) * n_v, c->stream);  // empty queue slots
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->adj_levels, 0, sizeof(int) * 4 + 6 * sizeof(float), c->stream);
     if (err) return err;
@@ -341,7 +400,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     time_begin(c, 4);
     k_adj_init<<<bl, th, 0, c->stream>>>(n_v, c->rec, dphi, c->mu, c->cnt, c->proc, c->ctl);
     k_adj_count<<<bl, th, 0, c->stream>>>(n_v, c->rec, c->tets, c->cnt);
-    k_adj_seed<<<bl, th, 0, c->stream>>>(n_v, c->cnt, c->proc, c->lists + n_v, c->ctl);
+    k_adj_seed<<<bl, th, 0, c->stream>>>(n_v, c->cnt, c->proc, c->lists, c->ctl);
     c->launches += 3;
     if ((err = cudaGetLastError())) return err;
     AdjArgs a;
@@ -369,11 +428,9 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.d_x = d_x;
     a.ctl = c->ctl;
     a.max_cycle_iters = 4096;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adjoint, 256, 0);
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 8) per_sm = 8;
-    int grid = per_sm * c->num_sms;
+    // one 256-thread CTA per SM: ~39k threads, several times the widest
+    // ready front, few enough that idle consumers poll lightly
+    int grid = c->num_sms;
     void *args[] = {&a};
     err = cudaLaunchCooperativeKernel((const void *)k_adjoint, dim3(grid), dim3(256), args, 0, c->stream);
     time_end(c, 4);

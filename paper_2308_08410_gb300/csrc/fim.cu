@@ -216,11 +216,19 @@ struct FimArgs {
 // atomic per CTA and iteration).  Reads of neighbour values may see this
 // iteration's updates (chaotic relaxation); the operator is monotone, so the
 // limit is the same fixed point.
-constexpr int FIM_G = 8;       // lanes per active vertex
+#ifndef GBP_FIM_G
+#define GBP_FIM_G 8  // lanes per active vertex
+#endif
+#ifndef GBP_FIM_BLOCK
+#define GBP_FIM_BLOCK 256  // threads per CTA
+#endif
+constexpr int FIM_G = GBP_FIM_G;
+constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
+constexpr int FIM_MINB = 1024 / GBP_FIM_BLOCK;  // CTAs per SM at 64 registers
 constexpr int FIM_CAP = 2048;  // per-CTA append buffer (overflow goes straight to global)
 
 template <int MODE>
-__global__ void __launch_bounds__(256, 4) k_fim(FimArgs a)
+__global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int sub = lane & (FIM_G - 1);
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(256, 4) k_fim(FimArgs a)
         __syncthreads();
         for (int q = threadIdx.x; q < s_cnt; q += blockDim.x) nlist[s_base + q] = s_list[q];
         ++nbar;
-        if (!grid_barrier(a.ctl, nbar * gridDim.x)) break;
+        if (!grid_barrier(a.ctl, nbar)) break;
     }
     // statistics
     unsigned int wf = my_faces;
@@ -380,7 +388,7 @@ __global__ void __launch_bounds__(256, 4) k_fim(FimArgs a)
 static int fim_grid(gbp_ctx *c, const void *fn)
 {
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, FIM_BLOCK, 0);
     if (per_sm < 1) per_sm = 1;
     return per_sm * c->num_sms;
 }
@@ -430,7 +438,7 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     int grid = fim_grid(c, fn);
     void *args[] = {&a};
     time_begin(c, 0);
-    err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, c->stream);
+    err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(FIM_BLOCK), args, 0, c->stream);
     time_end(c, 0);
     c->launches++;
     return err;

@@ -18,15 +18,30 @@ namespace gbp {
 // device control block (one per context)
 // ---------------------------------------------------------------------------
 struct Control {
-    int count[4];                 // active-list sizes (3 rotating lists) + spare
-    unsigned int barrier;         // grid-barrier arrivals (monotonic per launch)
+    // cache line 0: grid-barrier arrivals (atomics) and the abort flag
+    unsigned int barrier;         // arrivals, monotonic per launch
     int abort;                    // set when a bounded wait ran out
+    unsigned int pad0[30];
+    // cache line 1: grid-barrier release generation (polled by waiting CTAs)
+    unsigned int bar_gen;
+    unsigned int pad1[31];
+    // counters and statistics
+    int count[4];                 // active-list sizes (3 rotating lists) + spare
     int status;                   // latched gbp_status of the last device phase
     int iterations;               // FIM iterations of the last solve
     unsigned long long candidates;
     unsigned long long face_updates;
     unsigned long long fp64_fallbacks;
     unsigned long long unreached;
+    // work queue of the adjoint's dataflow phase: each counter on its own
+    // cache line (consumers, producers and the termination count do not
+    // contend)
+    int q_head;                   // tickets handed to consumers
+    int padq0[31];
+    int q_res;                    // slots reserved by producers
+    int padq1[31];
+    int q_active;                 // chains queued or in progress
+    int padq2[31];
     int adj_levels;
     int adj_cycle_nodes;
     int adj_cycle_iters;
@@ -335,30 +350,42 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p)
     return v;
 }
 
-// Returns false when the wait was abandoned (abort flag set by this or another
-// CTA).  `target` = (barrier index) * gridDim.x.  The spin is bounded: about
-// 2^22 polls with a short sleep each (well under a few seconds).
-__device__ __forceinline__ bool grid_barrier(Control *ctl, unsigned int target)
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier number `gen` (1, 2, ...) of a cooperative launch.  Each
+// CTA's thread 0 adds one arrival; the last arrival of this generation
+// publishes `gen` on a separate cache line, which the others poll (so the
+// polls do not contend with the arrival atomics).  The wait is bounded:
+// about 2^22 polls with a short sleep each; on timeout the abort flag and
+// GBP_ERR_TIMEOUT are set and every CTA leaves.  Returns false on abort.
+__device__ __forceinline__ bool grid_barrier(Control *ctl, unsigned int gen)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
         __threadfence();
-        atomicAdd(&ctl->barrier, 1u);
-        unsigned int spins = 0;
-        while (ld_acquire_u32(&ctl->barrier) < target) {
-            if (ld_relaxed_i32(&ctl->abort)) {
-                ok = 0;
-                break;
+        const unsigned int arrived = atomicAdd(&ctl->barrier, 1u) + 1u;
+        if (arrived == gen * gridDim.x) {
+            st_release_u32(&ctl->bar_gen, gen);
+        } else {
+            unsigned int spins = 0;
+            while (ld_acquire_u32(&ctl->bar_gen) < gen) {
+                if (ld_relaxed_i32(&ctl->abort)) {
+                    ok = 0;
+                    break;
+                }
+                if (++spins > (1u << 22)) {
+                    atomicExch(&ctl->abort, 1);
+                    atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(20);
             }
-            if (++spins > (1u << 22)) {
-                atomicExch(&ctl->abort, 1);
-                atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-            __nanosleep(64);
         }
         __threadfence();
         s_ok = ok;

@@ -61,11 +61,13 @@ def library_path() -> str:
 
 
 def load():
-    """Load libgbp.so, building it in place when missing or stale."""
+    """Load libgbp.so, building it in place when missing or stale.  The
+    environment variable GBP_LIBRARY selects another prebuilt copy of the
+    library (for example one compiled with different kernel shapes)."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.build()
+    path = os.environ.get("GBP_LIBRARY") or _build.build()
     L = C.CDLL(path)
     P, i32, i64, f32 = C.c_void_p, C.c_int32, C.c_int64, C.c_float
     sig = {
@@ -94,6 +96,17 @@ def load():
         "gbp_reset_kernel_times": ([P], i32),
         "gbp_launch_count": ([P], i64),
         "gbp_ecg_forward_noalloc": ([P, i32, i64, P, C.POINTER(Template), P, P], i32),
+        "gbp_nn_gemm_bf16": ([P, i32, i32, i32, P, i32, P, i32, P, i32, f32, f32], i32),
+        "gbp_nn_im2col": ([P, i32, i32, i32, i32, i32, i32, i32, P, P, i32], i32),
+        "gbp_nn_im2col_t": ([P, i32, i32, i32, i32, i32, i32, i32, P, i32, P, i32], i32),
+        "gbp_nn_col2im": ([P, i32, i32, i32, i32, i32, i32, i32, P, i32, P], i32),
+        "gbp_nn_bias_act": ([P, i32, i32, P, i32, P, P, i32], i32),
+        "gbp_nn_gelu_backward": ([P, i32, i32, P, i32, P], i32),
+        "gbp_nn_bias_grad": ([P, i32, i32, P, i32, P], i32),
+        "gbp_nn_cast_bf16": ([P, i32, i32, P, i32, P, i32], i32),
+        "gbp_nn_transpose_bf16": ([P, i32, i32, P, i32, P, i32], i32),
+        "gbp_nn_mse": ([P, i32, P, P, P, P], i32),
+        "gbp_nn_adam": ([P, i64, P, P, P, P, f32, f32, f32, f32, i32, P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -113,6 +126,9 @@ def exported_symbols():
         "gbp_forward_backward_host", "gbp_local_solve_batch", "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
         "gbp_ecg_forward_noalloc",
+        "gbp_nn_gemm_bf16", "gbp_nn_im2col", "gbp_nn_im2col_t", "gbp_nn_col2im", "gbp_nn_bias_act",
+        "gbp_nn_gelu_backward", "gbp_nn_bias_grad", "gbp_nn_cast_bf16", "gbp_nn_transpose_bf16",
+        "gbp_nn_mse", "gbp_nn_adam",
     ]
 
 
