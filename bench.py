@@ -300,8 +300,9 @@ def main():
         "tet_updates_per_s": world * face_updates * steps / total_s,
         "fim": {"iterations": st["iterations"], "face_updates": face_updates, "candidates": st["candidates"],
                 "fp64_fallbacks": st["fp64_fallbacks"], "ms": fim_ms},
-        "adjoint": {"levels": st["adj_levels"], "cycle_nodes": st["adj_cycle_nodes"],
+        "adjoint": {"seeds": st["adj_levels"], "cycle_nodes": st["adj_cycle_nodes"],
                     "cycle_iters": st["adj_cycle_iters"], "ms": adj_ms,
+                    "dataflow_ms": st["adj_dataflow_ms"], "cycle_ms": st["adj_cycle_ms"],
                     "roofline": {"bound": "hbm", "achieved": adj_achieved, "peak": peak, "unit": "GB/s",
                                  "frac": adj_achieved / peak}},
         "kernel_ms_per_step": {name: kt_ms[i] / steps for i, name in

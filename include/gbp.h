@@ -83,11 +83,13 @@ typedef struct {
     int64_t face_updates;   /* local problems solved (faces with a changed vertex) */
     int64_t fp64_fallbacks; /* local problems redone in FP64 */
     int64_t unreached;      /* vertices left at +inf */
-    int64_t adj_levels;     /* adjoint: topological levels */
+    int64_t adj_levels;     /* adjoint: vertices that seeded the dataflow (no children) */
     int64_t adj_cycle_nodes;/* adjoint: vertices solved by the cycle iteration */
     int64_t adj_cycle_iters;/* adjoint: iterations of the cycle iteration */
     int32_t status;         /* gbp_status of the last solve / backward */
     int32_t reserved;
+    double adj_dataflow_ms; /* adjoint: device time of the dataflow phase */
+    double adj_cycle_ms;    /* adjoint: device time of the cycle iteration */
 } gbp_solve_stats;
 
 /* Template action potential (Eq. tanh_waveform), read as
@@ -313,6 +315,13 @@ gbp_status gbp_get_kernel_times(gbp_ctx *ctx, int32_t n_classes, double *ms, int
 gbp_status gbp_reset_kernel_times(gbp_ctx *ctx);
 /* Total kernels this context launched since creation. */
 int64_t gbp_launch_count(gbp_ctx *ctx);
+
+/* Per-iteration trace of the FIM: when enabled, each solve records, per
+ * iteration, the number of active vertices and the GPU global timer (ns).
+ * gbp_get_trace synchronises and copies up to max_rows rows (int64 pairs)
+ * of the last solve into host memory `out`; returns the number of rows. */
+gbp_status gbp_enable_trace(gbp_ctx *ctx, int32_t on);
+int32_t gbp_get_trace(gbp_ctx *ctx, int64_t *out, int32_t max_rows);
 
 #ifdef __cplusplus
 }

@@ -195,6 +195,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     __syncthreads();
     bool ok = true;
     int mine = 0;
+    if (tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[0]));
     // ---- dataflow phase (no grid barrier per level) ----
     // The vertices readied so far sit in a work queue (lists[0..n_v), slots
     // start at -1).  Every thread takes tickets; the holder of ticket h
@@ -274,6 +275,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     if (threadIdx.x == 0 && s_proc) atomicAdd(&a.ctl->adj_processed, s_proc);
     ++nbar;
     if (!grid_barrier(a.ctl, nbar) || !ok) return;
+    if (tid == 0) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[1]));
+        a.ctl->adj_ts[2] = a.ctl->adj_ts[1];
+    }
     // ---- vertices blocked by cycles: fixed-point iteration ----
     // collect the unprocessed reached vertices R (closed under parents); the
     // barrier above ordered every write of the dataflow phase before this
@@ -357,6 +362,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[2]));
         a.ctl->adj_cycle_nodes = nR;
         a.ctl->adj_cycle_iters = it;
         if (it >= a.max_cycle_iters) atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_NOT_CONVERGED);

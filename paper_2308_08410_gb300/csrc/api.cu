@@ -213,6 +213,7 @@ void gbp_destroy(gbp_ctx *c)
     dfree(&c->dev_in);
     dfree(&c->dev_out);
     dfree(&c->loss_buf);
+    dfree(&c->trace);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     if (c->pin_in) cudaFreeHost(c->pin_in);
     if (c->pin_out) cudaFreeHost(c->pin_out);
@@ -489,6 +490,8 @@ gbp_status gbp_get_solve_stats(gbp_ctx *c, gbp_solve_stats *s)
     s->adj_cycle_iters = h.adj_cycle_iters;
     s->status = h.status ? h.status : h.param_status;
     s->reserved = 0;
+    s->adj_dataflow_ms = h.adj_ts[1] > h.adj_ts[0] ? (double)(h.adj_ts[1] - h.adj_ts[0]) * 1e-6 : 0.0;
+    s->adj_cycle_ms = h.adj_ts[2] > h.adj_ts[1] ? (double)(h.adj_ts[2] - h.adj_ts[1]) * 1e-6 : 0.0;
     return (gbp_status)s->status;
 }
 
@@ -650,5 +653,24 @@ gbp_status gbp_reset_kernel_times(gbp_ctx *c)
 }
 
 int64_t gbp_launch_count(gbp_ctx *c) { return c ? c->launches : 0; }
+
+gbp_status gbp_enable_trace(gbp_ctx *c, int32_t on)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    c->trace_on = on != 0;
+    return GBP_OK;
+}
+
+int32_t gbp_get_trace(gbp_ctx *c, int64_t *out, int32_t max_rows)
+{
+    if (!c || !out || max_rows < 1 || !c->trace) return 0;
+    DeviceGuard g(c->device);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return 0;
+    const int rows = max_rows < c->trace_cap ? max_rows : c->trace_cap;
+    if (cudaMemcpy(out, c->trace, sizeof(long long) * 2 * rows, cudaMemcpyDeviceToHost) != cudaSuccess) return 0;
+    int n = 0;
+    while (n < rows && out[2 * n + 1] != 0) ++n;
+    return n;
+}
 
 }  // extern "C"

@@ -203,6 +203,7 @@ struct FimArgs {
     float eps;
     int max_iters;
     int n_f;
+    long long *trace;  // optional: per iteration (active vertices, global timer ns)
 };
 
 // One iteration k = one Jacobi-style sweep of Algorithm 2 restricted to the
@@ -255,6 +256,12 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
     for (; k <= a.max_iters; ++k) {
         const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
         const int n_cand = ld_relaxed_i32(&a.ctl->count[cur]);
+        if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
+            unsigned long long tns;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tns));
+            a.trace[2 * (k - 1)] = n_cand;
+            a.trace[2 * (k - 1) + 1] = (long long)tns;
+        }
         if (n_cand == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.ctl->count[nn] = 0;
@@ -433,6 +440,20 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     a.eps = o->eps;
     a.max_iters = o->max_iters;
     a.n_f = o->n_f;
+    a.trace = nullptr;
+    if (c->trace_on) {
+        if (c->trace_cap < o->max_iters + 2) {
+            if (c->trace) cudaFree(c->trace);
+            c->trace = nullptr;
+            c->trace_cap = 0;
+            if (cudaMalloc(&c->trace, sizeof(long long) * 2 * (o->max_iters + 2)) == cudaSuccess)
+                c->trace_cap = o->max_iters + 2;
+        }
+        if (c->trace) {
+            cudaMemsetAsync(c->trace, 0, sizeof(long long) * 2 * c->trace_cap, c->stream);
+            a.trace = c->trace;
+        }
+    }
     const void *fn = o->local_solver == GBP_LOCAL_FISTA ? (const void *)k_fim<GBP_LOCAL_FISTA>
                                                         : (const void *)k_fim<GBP_LOCAL_EXACT>;
     int grid = fim_grid(c, fn);

@@ -48,6 +48,7 @@ struct Control {
     int adj_processed;
     float adj_delta[3];           // max |dx| of the cycle iteration (rotating slots)
     float adj_xmax[3];            // max |x| of the cycle iteration (rotating slots)
+    unsigned long long adj_ts[3]; // global timer at adjoint start, end of dataflow, end
     int pad[3];
     int param_status;             // latched by the metric precompute (kept across solves)
 };
@@ -474,6 +475,10 @@ struct gbp_ctx {
     int ev_cls[32];
     int64_t launches = 0;
     int sticky = 0;  // host-side latched status
+    // per-iteration FIM trace (optional)
+    bool trace_on = false;
+    long long *trace = nullptr;
+    int trace_cap = 0;
 };
 
 namespace gbp {

@@ -42,7 +42,8 @@ class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int64), ("candidates", C.c_int64), ("face_updates", C.c_int64),
                 ("fp64_fallbacks", C.c_int64), ("unreached", C.c_int64), ("adj_levels", C.c_int64),
                 ("adj_cycle_nodes", C.c_int64), ("adj_cycle_iters", C.c_int64),
-                ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("status", C.c_int32), ("reserved", C.c_int32), ("adj_dataflow_ms", C.c_double),
+                ("adj_cycle_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -96,6 +97,8 @@ def load():
         "gbp_reset_kernel_times": ([P], i32),
         "gbp_launch_count": ([P], i64),
         "gbp_ecg_forward_noalloc": ([P, i32, i64, P, C.POINTER(Template), P, P], i32),
+        "gbp_enable_trace": ([P, i32], i32),
+        "gbp_get_trace": ([P, P, i32], i32),
         "gbp_nn_gemm_bf16": ([P, i32, i32, i32, P, i32, P, i32, P, i32, f32, f32], i32),
         "gbp_nn_im2col": ([P, i32, i32, i32, i32, i32, i32, i32, P, P, i32], i32),
         "gbp_nn_im2col_t": ([P, i32, i32, i32, i32, i32, i32, i32, P, i32, P, i32], i32),
@@ -125,7 +128,7 @@ def exported_symbols():
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
         "gbp_forward_backward_host", "gbp_local_solve_batch", "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
-        "gbp_ecg_forward_noalloc",
+        "gbp_ecg_forward_noalloc", "gbp_enable_trace", "gbp_get_trace",
         "gbp_nn_gemm_bf16", "gbp_nn_im2col", "gbp_nn_im2col_t", "gbp_nn_col2im", "gbp_nn_bias_act",
         "gbp_nn_gelu_backward", "gbp_nn_bias_grad", "gbp_nn_cast_bf16", "gbp_nn_transpose_bf16",
         "gbp_nn_mse", "gbp_nn_adam",
@@ -331,6 +334,15 @@ class Context:
 
     def launch_count(self) -> int:
         return int(self.lib.gbp_launch_count(self.h))
+
+    def enable_trace(self, on=True):
+        _check(self.lib.gbp_enable_trace(self.h, int(bool(on))), "gbp_enable_trace")
+
+    def trace(self, max_rows=4096):
+        """(active vertices, global-timer ns) per FIM iteration of the last solve."""
+        buf = np.zeros((max_rows, 2), np.int64)
+        n = int(self.lib.gbp_get_trace(self.h, _hptr(buf), max_rows))
+        return buf[:n]
 
 
 @dataclasses.dataclass

@@ -252,3 +252,406 @@ class ConvMLP:
             else:
                 out.append(a)
         return out
+
+
+# ---------------------------------------------------------------------------
+# the c5 problem: cube mesh with a fast endocardial layer, surface sites
+# ---------------------------------------------------------------------------
+
+N_SITES = 10
+CF_RANGE, CT_RANGE, CE_RANGE, T_RANGE = (0.4, 0.8), (0.2, 0.4), (1.0, 3.0), (0.0, 20.0)
+
+
+@dataclasses.dataclass
+class C5:
+    """Cube mesh (c1 geometry) with a 1 mm fast layer on the z = 0 face whose
+    isotropic velocity c_endo is the third global velocity, 12 standard leads
+    from 10 electrodes on a 30 mm sphere, T = 300 @ 1 ms."""
+    problem: S.Problem
+    layer: np.ndarray        # bool [n_t]
+    surf_tet: np.ndarray     # int32 [F] tet owning each boundary triangle
+    surf_opp: np.ndarray     # int32 [F] slot of the tet vertex opposite the triangle
+    surf_tri: np.ndarray     # int32 [F, 3] vertex ids
+    side: float = 10.0
+
+
+def make_c5(n=20, side=10.0, T=300) -> C5:
+    mesh = S.kuhn_cube(n, side)
+    fib = S.fibres_cube(mesh, side)
+    zc = mesh.xyz.astype(np.float64)[mesh.tets][:, :, 2].mean(axis=1)
+    layer = zc < 1.0
+    el = S.fibonacci_sphere(10, 30.0, (side / 2,) * 3)
+    L = S.lead_field(mesh, el, S.twelve_lead_matrix())
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    f = mesh.tets[:, loc].reshape(-1, 3)
+    fs = np.sort(f, axis=1)
+    _, inv, cnt = np.unique(fs, axis=0, return_inverse=True, return_counts=True)
+    surf = np.nonzero(cnt[inv.ravel()] == 1)[0]
+    p = S.Problem("c5", mesh, fib, np.full(mesh.n_t, 0.6, np.float32), np.full(mesh.n_t, 0.3, np.float32),
+                  S.Onsets(S.ONSET_ELEMENT, np.zeros(N_SITES, np.int32), np.zeros(N_SITES, np.float32),
+                           np.full((N_SITES, 4), 0.25, np.float32)), L, S.Template(-80.0, 20.0, 1.0, 0.0, 1.0, T))
+    return C5(p, layer, (surf // 4).astype(np.int32), (surf % 4).astype(np.int32), f[surf].astype(np.int32), side)
+
+
+@dataclasses.dataclass
+class Params:
+    cf: float
+    ct: float
+    ce: float
+    tet: np.ndarray   # int32 [K]
+    bary: np.ndarray  # float32 [K, 4]
+    t: np.ndarray     # float32 [K]
+
+
+def sample_params(c5: C5, rng: np.random.Generator) -> Params:
+    """One draw of the prior: c_f ~ U[0.4,0.8], c_t ~ U[0.2,0.4],
+    c_endo ~ U[1,3], 10 surface sites, t ~ U[0,20]."""
+    fi = rng.choice(len(c5.surf_tet), size=N_SITES, replace=False)
+    b3 = 0.05 + 0.85 * rng.dirichlet(np.ones(3), size=N_SITES)
+    return Params(float(rng.uniform(*CF_RANGE)), float(rng.uniform(*CT_RANGE)), float(rng.uniform(*CE_RANGE)),
+                  c5.surf_tet[fi], _surface_bary(c5, fi, b3), rng.uniform(*T_RANGE, size=N_SITES).astype(np.float32))
+
+
+def _surface_bary(c5: C5, fi, b3):
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    b = np.zeros((len(fi), 4))
+    for k, f in enumerate(fi):
+        b[k, loc[c5.surf_opp[f]]] = b3[k]
+    return b.astype(np.float32)
+
+
+def site_xyz(c5: C5, prm: Params) -> np.ndarray:
+    V = c5.problem.mesh.xyz.astype(np.float64)[c5.problem.mesh.tets[prm.tet]]
+    return np.einsum("kq,kqr->kr", prm.bary.astype(np.float64), V)
+
+
+def encode(c5: C5, prm: Params) -> np.ndarray:
+    """Network target: sites sorted by onset time as (x, y, z)/side and
+    t / 20, then the three velocities scaled to [0, 1] by their priors."""
+    x = site_xyz(c5, prm)
+    o = np.argsort(prm.t, kind="stable")
+    out = np.concatenate([np.concatenate([x[o] / c5.side, (prm.t[o] / T_RANGE[1])[:, None]], axis=1).ravel(),
+                          [(prm.cf - CF_RANGE[0]) / (CF_RANGE[1] - CF_RANGE[0]),
+                           (prm.ct - CT_RANGE[0]) / (CT_RANGE[1] - CT_RANGE[0]),
+                           (prm.ce - CE_RANGE[0]) / (CE_RANGE[1] - CE_RANGE[0])]])
+    return out.astype(np.float32)
+
+
+def decode(c5: C5, y: np.ndarray) -> Params:
+    """Network output -> parameters: each site is moved to the closest point
+    of the mesh surface (nearest boundary triangle, clamped barycentric
+    coordinates); velocities clipped to their prior ranges."""
+    y = np.asarray(y, np.float64)
+    sites = y[:4 * N_SITES].reshape(N_SITES, 4)
+    xyz = np.clip(sites[:, :3] * c5.side, 0.0, c5.side)
+    t = np.clip(sites[:, 3] * T_RANGE[1], -5.0, 40.0).astype(np.float32)
+    X = c5.problem.mesh.xyz.astype(np.float64)
+    tri = X[c5.surf_tri]  # [F, 3, 3]
+    cen = tri.mean(axis=1)
+    fi = np.argmin(((xyz[:, None, :] - cen[None]) ** 2).sum(-1), axis=1)
+    b3 = np.zeros((N_SITES, 3))
+    for k in range(N_SITES):
+        b3[k] = _closest_bary(tri[fi[k]], xyz[k])
+    b3 = 0.02 + 0.94 * b3
+    cf = float(np.clip(CF_RANGE[0] + y[40] * (CF_RANGE[1] - CF_RANGE[0]), 0.3, 1.0))
+    ct = float(np.clip(CT_RANGE[0] + y[41] * (CT_RANGE[1] - CT_RANGE[0]), 0.15, 0.6))
+    ce = float(np.clip(CE_RANGE[0] + y[42] * (CE_RANGE[1] - CE_RANGE[0]), 0.5, 4.0))
+    return Params(cf, ct, ce, c5.surf_tet[fi], _surface_bary(c5, fi, b3), t)
+
+
+def _closest_bary(tri, p):
+    """Barycentric coordinates of the point of triangle tri closest to p
+    (projection onto the plane, then clamping onto the simplex)."""
+    a, b, c = tri
+    v0, v1, v2 = b - a, c - a, p - a
+    G = np.array([[v0 @ v0, v0 @ v1], [v0 @ v1, v1 @ v1]])
+    rhs = np.array([v2 @ v0, v2 @ v1])
+    try:
+        s, u = np.linalg.solve(G, rhs)
+    except np.linalg.LinAlgError:
+        s, u = 1 / 3, 1 / 3
+    w = np.array([1 - s - u, s, u])
+    w = np.clip(w, 0, None)
+    return w / w.sum() if w.sum() > 0 else np.full(3, 1 / 3)
+
+
+def default_params(c5: C5, rng: np.random.Generator) -> Params:
+    """Plain Geodesic-BP start: prior-mean velocities, 10 random surface sites
+    at t = 10 ms."""
+    fi = rng.choice(len(c5.surf_tet), size=N_SITES, replace=False)
+    b3 = np.full((N_SITES, 3), 1 / 3)
+    return Params(0.6, 0.3, 2.0, c5.surf_tet[fi], _surface_bary(c5, fi, b3), np.full(N_SITES, 10.0, np.float32))
+
+
+class C5Device:
+    """The c5 problem uploaded to a context, with helpers to run the forward
+    model for one parameter set."""
+
+    def __init__(self, ctx: gbp.Context, c5: C5):
+        self.ctx, self.c5 = ctx, c5
+        self.dp = gbp.setup_problem(ctx, c5.problem)
+        dev = ctx.torch_device
+        self.layer = torch.from_numpy(c5.layer).to(dev)
+        self.n_t = c5.problem.mesh.n_t
+        self.phi = torch.empty(c5.problem.mesh.n_v, device=dev)
+        self.ecg = torch.empty(c5.problem.L.shape[0], c5.problem.tmpl.T, device=dev)
+
+    def velocities(self, cf, ct, ce):
+        """Per-tet velocities (torch, differentiable in the three globals)."""
+        one = torch.ones(self.n_t, device=self.ctx.torch_device)
+        cft = torch.where(self.layer, ce * one, cf * one)
+        ctt = torch.where(self.layer, ce * one, ct * one)
+        return cft.contiguous(), ctt.contiguous()
+
+    def simulate(self, prm: Params, precision=gbp.PREC_FP32):
+        dev = self.ctx.torch_device
+        cf, ct = self.velocities(torch.tensor(prm.cf, device=dev), torch.tensor(prm.ct, device=dev),
+                                 torch.tensor(prm.ce, device=dev))
+        self.ctx.set_velocities(cf, ct)
+        self.ctx.set_onsets(gbp.ONSET_ELEMENT, torch.from_numpy(prm.tet).to(dev), torch.from_numpy(prm.t).to(dev),
+                            torch.from_numpy(prm.bary).to(dev))
+        self.ctx.eikonal_solve(phi=self.phi)
+        return self.ctx.ecg_forward(self.phi, self.c5.problem.tmpl, precision=precision, out=self.ecg)
+
+
+def generate(dev_c5: C5Device, n: int, seed: int):
+    """n (ECG, target) pairs from the forward model: ECG [n, T, 12]
+    (channels-last), targets [n, 43], and the parameter sets."""
+    rng = np.random.default_rng(seed)
+    T = dev_c5.c5.problem.tmpl.T
+    X = np.empty((n, T, 12), np.float32)
+    Y = np.empty((n, 43), np.float32)
+    P = []
+    for i in range(n):
+        prm = sample_params(dev_c5.c5, rng)
+        V = dev_c5.simulate(prm)
+        X[i] = V.t().cpu().numpy()
+        Y[i] = encode(dev_c5.c5, prm)
+        P.append(prm)
+    return X, Y, P
+
+
+def he_init(cfg: NetConfig, seed: int):
+    """Seeded He-normal weights, zero biases, in the reference layout."""
+    rng = np.random.default_rng(seed)
+    ps = []
+    cin = cfg.C_in
+    flat = cfg.lens()[-1] * cfg.channels
+    shapes = []
+    for _ in range(cfg.n_conv):
+        shapes += [(cfg.channels, cfg.ksize, cin), (cfg.channels,)]
+        cin = cfg.channels
+    shapes += [(cfg.hidden, flat), (cfg.hidden,), (cfg.n_out, cfg.hidden), (cfg.n_out,)]
+    for shp in shapes:
+        if len(shp) == 1:
+            ps.append(np.zeros(shp, np.float32))
+        else:
+            fan_in = int(np.prod(shp[1:]))
+            ps.append((rng.standard_normal(shp) * math.sqrt(2.0 / fan_in)).astype(np.float32))
+    return ps
+
+
+def train(ctx: gbp.Context, X: np.ndarray, Y: np.ndarray, epochs=30, batch=256, lr=1e-3, seed=0, x_scale=None,
+          X_val=None, Y_val=None, log=None):
+    """Adam on the MSE with the project's kernels only.  Returns
+    (net, x_scale, history) with history rows (epoch, train loss, val loss, s)."""
+    cfg = NetConfig(C_in=X.shape[2], L_in=X.shape[1], n_out=Y.shape[1])
+    if x_scale is None:
+        x_scale = float(1.0 / max(np.sqrt(np.mean(X.astype(np.float64) ** 2)), 1e-12))
+    net = ConvMLP(ctx, cfg, he_init(cfg, seed), max_batch=batch)
+    dev = ctx.torch_device
+    Xd = torch.from_numpy(X).to(dev) * x_scale
+    Yd = torch.from_numpy(Y).to(dev)
+    rng = np.random.default_rng(seed + 1)
+    n = X.shape[0]
+    hist = []
+    t0 = time.perf_counter()
+    steps_per_epoch = max(1, n // batch)
+    total = epochs * steps_per_epoch
+    step = 0
+    for ep in range(epochs):
+        perm = torch.from_numpy(rng.permutation(n)).to(dev)
+        acc = torch.zeros(1, device=dev)
+        for s in range(steps_per_epoch):
+            idx = perm[s * batch:(s + 1) * batch]
+            net.forward(Xd[idx], batch)
+            acc += net.mse(Yd[idx].contiguous(), batch)
+            net.backward(net.dy[:batch], batch)
+            # cosine decay of the learning rate
+            lr_s = lr * 0.5 * (1.0 + math.cos(math.pi * step / total))
+            net.adam_step(lr=lr_s)
+            step += 1
+        vl = evaluate_loss(net, X_val, Y_val, x_scale, batch) if X_val is not None else float("nan")
+        hist.append((ep, float(acc.item()) / steps_per_epoch, vl, time.perf_counter() - t0))
+        if log:
+            log(hist[-1])
+    torch.cuda.synchronize()
+    return net, x_scale, hist
+
+
+def predict(net: ConvMLP, X: np.ndarray, x_scale: float, batch: int = 256) -> np.ndarray:
+    dev = net.ctx.torch_device
+    out = np.empty((X.shape[0], net.cfg.n_out), np.float32)
+    for s in range(0, X.shape[0], batch):
+        xb = torch.from_numpy(X[s:s + batch]).to(dev) * x_scale
+        out[s:s + len(xb)] = net.forward(xb.contiguous(), len(xb)).cpu().numpy()
+    return out
+
+
+def evaluate_loss(net: ConvMLP, X, Y, x_scale, batch=256):
+    if X is None:
+        return float("nan")
+    P = predict(net, X, x_scale, batch)
+    return float(np.mean((P.astype(np.float64) - Y) ** 2))
+
+
+# ---------------------------------------------------------------------------
+# Geodesic-BP refinement with three global velocities and the onsets
+# ---------------------------------------------------------------------------
+
+class C5Inverse:
+    """Adam over (c_f, c_t, c_endo, onset times, onset positions inside their
+    tets) with the loss and gradient of the C ABI (GeodesicEcgLoss)."""
+
+    def __init__(self, dev_c5: C5Device, target_ecg: np.ndarray, init: Params, precision=gbp.PREC_FP32,
+                 opts=None):
+        from .inverse import EvalOp
+        self.d = dev_c5
+        ctx = dev_c5.ctx
+        dv = ctx.torch_device
+        c5 = dev_c5.c5
+        self.log_c = torch.tensor(np.log([init.cf, init.ct, init.ce]), dtype=torch.float32, device=dv,
+                                  requires_grad=True)
+        self.t = torch.tensor(init.t, dtype=torch.float32, device=dv, requires_grad=True)
+        V = c5.problem.mesh.xyz.astype(np.float64)[c5.problem.mesh.tets[init.tet]]
+        x0 = np.einsum("kq,kqr->kr", init.bary.astype(np.float64), V)
+        M = np.concatenate([V.transpose(0, 2, 1), np.ones((N_SITES, 1, 4))], axis=1)
+        self.Vt_inv = torch.tensor(np.linalg.inv(M), dtype=torch.float32, device=dv)
+        self.Vt = torch.tensor(V, dtype=torch.float32, device=dv)
+        self.x = torch.tensor(x0.astype(np.float32), device=dv, requires_grad=True)
+        n_v = c5.problem.mesh.n_v
+        self.op = EvalOp(ctx=ctx, kind=gbp.ONSET_ELEMENT, on_idx=torch.from_numpy(init.tet).to(dv),
+                         target=torch.from_numpy(np.ascontiguousarray(target_ecg, np.float32)).to(dv),
+                         tmpl=c5.problem.tmpl, opts=opts if opts is not None else gbp.make_opts(),
+                         precision=precision, phi=torch.empty(n_v, device=dv),
+                         parent=torch.empty(n_v, dtype=torch.int32, device=dv),
+                         alpha=torch.empty(n_v, 3, device=dv),
+                         ecg=torch.empty(c5.problem.L.shape[0], c5.problem.tmpl.T, device=dv))
+
+    def bary(self):
+        xh = torch.cat([self.x.detach(), torch.ones_like(self.x[:, :1])], dim=1)
+        return torch.einsum("kij,kj->ki", self.Vt_inv, xh).contiguous()
+
+    def loss(self):
+        from .inverse import GeodesicEcgLoss
+        c = torch.exp(self.log_c)
+        cf, ct = self.d.velocities(c[0], c[1], c[2])
+        return GeodesicEcgLoss.apply(cf, ct, self.t, self.x, self.bary(), self.op)
+
+    @torch.no_grad()
+    def project(self, floor=1e-3):
+        b = self.bary().clamp_min(floor)
+        b = b / b.sum(dim=1, keepdim=True)
+        self.x.copy_(torch.einsum("kq,kqr->kr", b, self.Vt))
+
+    def run(self, iters, lr=2e-2, stop_at=None, time_budget=None):
+        """Adam; returns [(iteration, loss, seconds)], stopping early once the
+        loss is <= stop_at or after time_budget seconds."""
+        opt = torch.optim.Adam([self.log_c, self.t, self.x], lr=lr)
+        hist = []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for it in range(iters):
+            opt.zero_grad(set_to_none=True)
+            loss = self.loss()
+            loss.backward()
+            opt.step()
+            self.project()
+            lv = float(loss.item())
+            hist.append((it, lv, time.perf_counter() - t0))
+            if stop_at is not None and lv <= stop_at:
+                break
+            if time_budget is not None and hist[-1][2] > time_budget:
+                break
+        return hist
+
+
+# ---------------------------------------------------------------------------
+# the experiment: learned init + BF16 ECG vs default-init plain Geodesic-BP
+# ---------------------------------------------------------------------------
+
+def run_experiment(n_train=20000, n_test=2000, epochs=30, n_eval=20, iters=300, lr_refine=2e-2, seed=0,
+                   noise=0.05, log=print):
+    """Generate the data with the forward model, train the network, then for
+    n_eval held-out noisy ECGs run (a) plain Geodesic-BP from the default
+    start with the FP32 ECG and (b) Geodesic-BP from the network's prediction
+    with the BF16 tensor-core ECG until it reaches (a)'s best misfit.
+    Returns a dict of timings, losses and activation errors."""
+    ctx = gbp.Context(0)
+    c5 = make_c5()
+    d = C5Device(ctx, c5)
+    t0 = time.perf_counter()
+    X, Y, _ = generate(d, n_train, seed + 1)
+    Xv, Yv, Pv = generate(d, n_test, seed + 2)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t0
+    log(f"generated {n_train}+{n_test} pairs in {t_gen:.1f} s")
+    net, xs, hist = train(ctx, X, Y, epochs=epochs, X_val=Xv, Y_val=Yv,
+                          log=lambda h: log(f"epoch {h[0]} train {h[1]:.4e} val {h[2]:.4e} {h[3]:.1f}s"))
+    t_train = hist[-1][3]
+    rng = np.random.default_rng(seed + 3)
+    rows = []
+    for i in range(n_eval):
+        truth = Pv[i]
+        clean = d.simulate(truth).cpu().numpy()
+        phi_true = d.phi.cpu().numpy().copy()
+        target = S.add_noise(clean, noise, seed + 100 + i)
+        # (a) plain
+        inv_p = C5Inverse(d, target, default_params(c5, rng), precision=gbp.PREC_FP32)
+        hp = inv_p.run(iters, lr=lr_refine)
+        best = min(range(len(hp)), key=lambda k: hp[k][1])
+        m_plain, t_plain = hp[best][1], hp[best][2]
+        phi_p = inv_p.op.phi.cpu().numpy().copy()
+        # (b) learned init + BF16 ECG
+        torch.cuda.synchronize()
+        ti = time.perf_counter()
+        xin = np.ascontiguousarray(target.T[None].astype(np.float32))
+        init = decode(c5, predict(net, xin, xs)[0])
+        t_inf = time.perf_counter() - ti
+        inv_l = C5Inverse(d, target, init, precision=gbp.PREC_BF16)
+        hl = inv_l.run(iters, lr=lr_refine, stop_at=m_plain)
+        reached = [h for h in hl if h[1] <= m_plain]
+        t_learned = (reached[0][2] if reached else float("inf")) + t_inf
+        phi_l = inv_l.op.phi.cpu().numpy().copy()
+        rmse = lambda a: float(np.sqrt(np.mean((a - phi_true) ** 2)))  # noqa: E731
+        rows.append(dict(case=i, plain_loss0=hp[0][1], learned_loss0=hl[0][1], plain_best=m_plain,
+                         plain_iters=best + 1, plain_time=t_plain, learned_iters=len(hl), learned_time=t_learned,
+                         learned_final=hl[-1][1], plain_rmse=rmse(phi_p), learned_rmse=rmse(phi_l)))
+        log(rows[-1])
+    med = lambda k: float(np.median([r[k] for r in rows]))  # noqa: E731
+    return dict(n_train=n_train, n_test=n_test, epochs=epochs, gen_s=t_gen, train_s=t_train,
+                val_mse=hist[-1][2], cases=rows,
+                median=dict(plain_time=med("plain_time"), learned_time=med("learned_time"),
+                            plain_loss0=med("plain_loss0"), learned_loss0=med("learned_loss0"),
+                            plain_rmse=med("plain_rmse"), learned_rmse=med("learned_rmse")),
+                reached=sum(np.isfinite(r["learned_time"]) for r in rows))
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="learned initialiser + BF16 ECG vs plain Geodesic-BP (c5)")
+    ap.add_argument("--train", type=int, default=20000)
+    ap.add_argument("--test", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--eval", type=int, default=20)
+    ap.add_argument("--iters", type=int, default=300)
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    res = run_experiment(a.train, a.test, a.epochs, a.eval, a.iters)
+    s = json.dumps(res)
+    print(s)
+    if a.out:
+        with open(a.out, "w") as f:
+            f.write(s)
