@@ -144,6 +144,14 @@ static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0
     return true;
 }
 
+// The interior step is redone in FP64 when 1 - Delta^T Q^-1 Delta falls below
+// this value (or the face is nearly degenerate).  The candidate is always
+// evaluated at its own (feasible) point, so an FP32 location error only costs
+// second order in the value.
+#ifndef GBP_FP64_FALLBACK_TOL
+#define GBP_FP64_FALLBACK_TOL 1e-3f
+#endif
+
 // Exact minimiser of Eq. (upwind_eq_lsqr) on one face (Sec. II-B).  The
 // objective is convex on the simplex, so the minimum is at a KKT point:
 // the stationary point of the face interior, of an edge, or a vertex.  All
@@ -201,7 +209,7 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
         if (k < 1.f || degenerate) {
             float b0, b1;
             bool found = false;
-            if (degenerate || 1.f - k < 1e-3f) {
+            if (degenerate || 1.f - k < GBP_FP64_FALLBACK_TOL) {
                 ++*fb;
                 found = interior_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, ph[0],
                                       ph[1], ph[2], &b0, &b1);

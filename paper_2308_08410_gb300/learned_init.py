@@ -630,11 +630,11 @@ def run_experiment(n_train=20000, n_test=2000, epochs=30, n_eval=20, iters=300, 
         log(rows[-1])
     med = lambda k: float(np.median([r[k] for r in rows]))  # noqa: E731
     return dict(n_train=n_train, n_test=n_test, epochs=epochs, gen_s=t_gen, train_s=t_train,
-                val_mse=hist[-1][2], cases=rows,
+                val_mse=float(hist[-1][2]), cases=rows,
                 median=dict(plain_time=med("plain_time"), learned_time=med("learned_time"),
                             plain_loss0=med("plain_loss0"), learned_loss0=med("learned_loss0"),
                             plain_rmse=med("plain_rmse"), learned_rmse=med("learned_rmse")),
-                reached=sum(np.isfinite(r["learned_time"]) for r in rows))
+                reached=int(sum(bool(np.isfinite(r["learned_time"])) for r in rows)))
 
 
 if __name__ == "__main__":
