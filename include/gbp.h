@@ -179,7 +179,8 @@ gbp_status gbp_ecg_forward(gbp_ctx *ctx, const float *phi, const gbp_template *t
  * loss = 1/(N T) sum_{l,s} (ecg - target)^2, and its derivative with respect
  * to each phi_n (Sec. II-D: nabla V = -B^T U' nabla phi).  phi, ecg (from
  * gbp_ecg_forward), target device float32; loss device float32 [1];
- * dphi device float32 [n_v]. */
+ * dphi device float32 [n_v].  N * T <= 51200 (the residual is staged in
+ * shared memory). */
 gbp_status gbp_ecg_loss_backward(gbp_ctx *ctx, const float *phi, const float *ecg,
                                  const float *target, const gbp_template *tmpl, float *loss,
                                  float *dphi);

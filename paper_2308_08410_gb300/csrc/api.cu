@@ -509,6 +509,7 @@ gbp_status gbp_ecg_loss_backward(gbp_ctx *c, const float *phi, const float *ecg,
 {
     if (!c || !phi || !ecg || !target || !loss || !dphi || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
     if (!c->N) return GBP_ERR_STATE;
+    if ((int64_t)c->N * tmpl->T > 51200) return GBP_ERR_INVALID_ARG;
     DeviceGuard g(c->device);
     return from_cuda(gbp::launch_ecg_backward(c, phi, ecg, target, tmpl, loss, dphi));
 }

@@ -19,15 +19,18 @@ __device__ __forceinline__ float logistic(float z) { return __fdividef(1.f, 1.f 
 
 // Per CTA: a contiguous vertex range; thread (s_loc, g) accumulates sample
 // s = s_base + s_loc over the vertices q = g mod G of each staged chunk.
-// Writes part[cta][l][s] (deterministic second-stage reduction).
-__global__ void __launch_bounds__(512) k_ecg_fwd(int64_t n_v, int N, int T, const float *__restrict__ L,
-                                                 const float *__restrict__ phi, float t0, float dt, float c4,
-                                                 int T_tile, int G, int64_t per_cta, float *__restrict__ part)
+// Writes part[cta][l][s] (deterministic second-stage reduction).  NL is the
+// number of leads, a compile-time constant so the accumulators stay in
+// registers.
+template <int NL>
+__global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const float *__restrict__ L,
+                                                   const float *__restrict__ phi, float t0, float dt, float c4,
+                                                   int T_tile, int G, int64_t per_cta, float *__restrict__ part)
 {
     extern __shared__ float sm[];
     float *sphi = sm;               // [ECG_CH]
-    float *sL = sm + ECG_CH;        // [N][ECG_CH]
-    float *red = sL + N * ECG_CH;   // [G][N][T_tile]
+    float *sL = sm + ECG_CH;        // [ECG_CH][NL] (vertex-major: one float4 row per vertex)
+    float *red = sL + NL * ECG_CH;  // [G][NL][T_tile]
     const int tid = threadIdx.x;
     const int s_loc = tid % T_tile;
     const int g = tid / T_tile;
@@ -36,41 +39,65 @@ __global__ void __launch_bounds__(512) k_ecg_fwd(int64_t n_v, int N, int T, cons
     for (int s_base = 0; s_base < T; s_base += T_tile) {
         const int s = s_base + s_loc;
         const float ts = fmaf((float)s, dt, t0);
-        float acc[ECG_NL];
+        float acc[NL];
 #pragma unroll
-        for (int l = 0; l < ECG_NL; ++l) acc[l] = 0.f;
+        for (int l = 0; l < NL; ++l) acc[l] = 0.f;
         for (int64_t c0 = n0; c0 < n1; c0 += ECG_CH) {
             const int cnt = (int)min((int64_t)ECG_CH, n1 - c0);
             __syncthreads();
             for (int q = tid; q < ECG_CH; q += blockDim.x) sphi[q] = q < cnt ? phi[c0 + q] : GBP_INF;
-            for (int e = tid; e < N * ECG_CH; e += blockDim.x) {
-                int l = e / ECG_CH, q = e - l * ECG_CH;
-                sL[e] = q < cnt ? __ldg(&L[(int64_t)l * n_v + c0 + q]) : 0.f;
+            for (int e = tid; e < NL * ECG_CH; e += blockDim.x) {
+                const int l = e / ECG_CH, q = e - l * ECG_CH;
+                sL[q * NL + l] = q < cnt ? __ldg(&L[(int64_t)l * n_v + c0 + q]) : 0.f;
             }
             __syncthreads();
             if (s < T) {
                 for (int q = g; q < cnt; q += G) {
                     const float sg = logistic((ts - sphi[q]) * c4);
-                    if (sg == 0.f) continue;
+                    const float *Lq = sL + q * NL;
 #pragma unroll
-                    for (int l = 0; l < ECG_NL; ++l)
-                        if (l < N) acc[l] = fmaf(sL[l * ECG_CH + q], sg, acc[l]);
+                    for (int l = 0; l < NL; ++l) acc[l] = fmaf(Lq[l], sg, acc[l]);
                 }
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int l = 0; l < ECG_NL; ++l)
-            if (l < N) red[(g * N + l) * T_tile + s_loc] = acc[l];
+        for (int l = 0; l < NL; ++l) red[(g * NL + l) * T_tile + s_loc] = acc[l];
         __syncthreads();
-        for (int e = tid; e < N * T_tile; e += blockDim.x) {
-            int l = e / T_tile, sl = e - l * T_tile;
+        for (int e = tid; e < NL * T_tile; e += blockDim.x) {
+            const int l = e / T_tile, sl = e - l * T_tile;
             if (s_base + sl >= T) continue;
             float v = 0.f;
-            for (int gg = 0; gg < G; ++gg) v += red[(gg * N + l) * T_tile + sl];
-            part[((int64_t)blockIdx.x * N + l) * T + s_base + sl] = v;
+            for (int gg = 0; gg < G; ++gg) v += red[(gg * NL + l) * T_tile + sl];
+            part[((int64_t)blockIdx.x * NL + l) * T + s_base + sl] = v;
         }
     }
+}
+
+template <int NL>
+static cudaError_t launch_fwd_n(int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
+                                const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
+                                int64_t per, float *part)
+{
+    cudaFuncSetAttribute(k_ecg_fwd_t<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ecg_fwd_t<NL><<<ncta, threads, smem, st>>>(n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part);
+    return cudaGetLastError();
+}
+
+// one instantiation per lead count 1..16
+cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
+                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
+                                 int64_t per, float *part)
+{
+    switch (N) {
+#define GBP_ECG_CASE(n) \
+    case n: return launch_fwd_n<n>(ncta, threads, smem, st, n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part);
+        GBP_ECG_CASE(1) GBP_ECG_CASE(2) GBP_ECG_CASE(3) GBP_ECG_CASE(4) GBP_ECG_CASE(5) GBP_ECG_CASE(6)
+        GBP_ECG_CASE(7) GBP_ECG_CASE(8) GBP_ECG_CASE(9) GBP_ECG_CASE(10) GBP_ECG_CASE(11) GBP_ECG_CASE(12)
+        GBP_ECG_CASE(13) GBP_ECG_CASE(14) GBP_ECG_CASE(15) GBP_ECG_CASE(16)
+#undef GBP_ECG_CASE
+    }
+    return cudaErrorInvalidValue;
 }
 
 // V[l][s] = K0 S_l + (K1 - K0) sum_cta part[cta][l][s]  (fixed order)
@@ -116,11 +143,11 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
         c->ecg_part_cap = need;
     }
     size_t smem = sizeof(float) * (ECG_CH + (size_t)N * ECG_CH + (size_t)G * N * T_tile);
-    cudaFuncSetAttribute(k_ecg_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     float c4 = 4.f / t->tau;
     time_begin(c, 2);
-    k_ecg_fwd<<<ncta, T_tile * G, smem, c->stream>>>(c->n_v, N, T, c->L, phi, t->t0, t->dt, c4, T_tile, G, per,
-                                                    c->ecg_part);
+    cudaError_t le = launch_ecg_fwd_leads(N, ncta, T_tile * G, smem, c->stream, c->n_v, T, c->L, phi, t->t0, t->dt,
+                                          c4, T_tile, G, per, c->ecg_part);
+    if (le) return le;
     k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, c->stream>>>(N, T, ncta, c->ecg_part, c->Lrowsum, t->K0,
                                                             t->K1 - t->K0, ecg);
     time_end(c, 2);
@@ -154,28 +181,31 @@ __global__ void k_ecg_resid(int NT, const float *__restrict__ ecg, const float *
 
 // lam_n = -2/(N T) (K1-K0)(4/tau) sum_s sigma(1-sigma)(z_s) sum_l B_ln r_l(s),
 // z_s = 4 (t_s - phi_n)/tau.  Samples with |z| > 80 carry a weight below
-// 2e-35 and are skipped (their terms vanish against the FP32 sum).
-__global__ void __launch_bounds__(256) k_ecg_bwd(int64_t n_v, int N, int T, const float *__restrict__ L,
-                                                 const float *__restrict__ phi, const float *__restrict__ r,
-                                                 int r_in_smem, float t0, float dt, float tau, float scale,
-                                                 float *__restrict__ dphi)
+// 2e-35 and are skipped (their terms vanish against the FP32 sum).  The
+// residual is stored sample-major in shared memory (rT[s][l]) so one sample's
+// leads are contiguous.  NL = number of leads (compile time).
+template <int NL>
+__global__ void __launch_bounds__(256) k_ecg_bwd_t(int64_t n_v, int T, const float *__restrict__ L,
+                                                   const float *__restrict__ phi, const float *__restrict__ r,
+                                                   float t0, float dt, float tau, float scale,
+                                                   float *__restrict__ dphi)
 {
-    extern __shared__ float sr[];
-    if (r_in_smem) {
-        for (int e = threadIdx.x; e < N * T; e += blockDim.x) sr[e] = r[e];
-        __syncthreads();
+    extern __shared__ float rT[];  // [T][NL]
+    for (int e = threadIdx.x; e < NL * T; e += blockDim.x) {
+        const int l = e / T, s = e - l * T;
+        rT[s * NL + l] = r[e];
     }
-    const float *rr = r_in_smem ? sr : r;
-    int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    __syncthreads();
+    const int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (n >= n_v) return;
-    float p = phi[n];
+    const float p = phi[n];
     if (!(p < GBP_INF)) {
         dphi[n] = 0.f;
         return;
     }
-    float Ln[ECG_NL];
+    float Ln[NL];
 #pragma unroll
-    for (int l = 0; l < ECG_NL; ++l) Ln[l] = l < N ? __ldg(&L[(int64_t)l * n_v + n]) : 0.f;
+    for (int l = 0; l < NL; ++l) Ln[l] = __ldg(&L[(int64_t)l * n_v + n]);
     const float c4 = 4.f / tau;
     const float win = 20.f * tau;
     // clamp in float before converting, so huge phi cannot overflow the int
@@ -183,16 +213,26 @@ __global__ void __launch_bounds__(256) k_ecg_bwd(int64_t n_v, int N, int T, cons
     const int s_hi = (int)fminf(fmaxf(floorf((p + win - t0) / dt), -1.f), (float)(T - 1));
     float acc = 0.f;
     for (int s = s_lo; s <= s_hi; ++s) {
-        float z = (fmaf((float)s, dt, t0) - p) * c4;
-        float e = __expf(-fabsf(z));
-        float w = __fdividef(e, (1.f + e) * (1.f + e));
+        const float z = (fmaf((float)s, dt, t0) - p) * c4;
+        const float e = __expf(-fabsf(z));
+        const float w = __fdividef(e, (1.f + e) * (1.f + e));
+        const float *rs = rT + s * NL;
         float cs = 0.f;
 #pragma unroll
-        for (int l = 0; l < ECG_NL; ++l)
-            if (l < N) cs = fmaf(Ln[l], rr[l * T + s], cs);
+        for (int l = 0; l < NL; ++l) cs = fmaf(Ln[l], rs[l], cs);
         acc = fmaf(w, cs, acc);
     }
     dphi[n] = scale * acc;
+}
+
+template <int NL>
+static cudaError_t launch_bwd_n(unsigned blocks, size_t smem, cudaStream_t st, int64_t n_v, int T, const float *L,
+                                const float *phi, const float *r, float t0, float dt, float tau, float scale,
+                                float *dphi)
+{
+    cudaFuncSetAttribute(k_ecg_bwd_t<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_ecg_bwd_t<NL><<<blocks, 256, smem, st>>>(n_v, T, L, phi, r, t0, dt, tau, scale, dphi);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, const float *target,
@@ -212,15 +252,21 @@ cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, 
     }
     time_begin(c, 3);
     k_ecg_resid<<<1, 1024, 0, c->stream>>>((int)NT, ecg, target, c->resid, 1.f / (float)NT, loss);
-    size_t smem = sizeof(float) * NT;
-    int in_smem = smem <= 160 * 1024;
-    if (in_smem) cudaFuncSetAttribute(k_ecg_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    else smem = 0;
+    size_t smem = sizeof(float) * NT;  // N * T <= 16 * 4096 floats = 256 KB at most
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
     float scale = -2.f / (float)NT * (t->K1 - t->K0) * (4.f / t->tau);
-    int th = 256;
-    k_ecg_bwd<<<(unsigned)((c->n_v + th - 1) / th), th, smem, c->stream>>>(c->n_v, N, T, c->L, phi, c->resid,
-                                                                           in_smem, t->t0, t->dt, t->tau, scale,
-                                                                           dphi);
+    const unsigned blocks = (unsigned)((c->n_v + 255) / 256);
+    cudaError_t le = cudaErrorInvalidValue;
+    switch (N) {
+#define GBP_BWD_CASE(n) \
+    case n: le = launch_bwd_n<n>(blocks, smem, c->stream, c->n_v, T, c->L, phi, c->resid, t->t0, t->dt, t->tau, \
+                                 scale, dphi); break;
+        GBP_BWD_CASE(1) GBP_BWD_CASE(2) GBP_BWD_CASE(3) GBP_BWD_CASE(4) GBP_BWD_CASE(5) GBP_BWD_CASE(6)
+        GBP_BWD_CASE(7) GBP_BWD_CASE(8) GBP_BWD_CASE(9) GBP_BWD_CASE(10) GBP_BWD_CASE(11) GBP_BWD_CASE(12)
+        GBP_BWD_CASE(13) GBP_BWD_CASE(14) GBP_BWD_CASE(15) GBP_BWD_CASE(16)
+#undef GBP_BWD_CASE
+    }
+    if (le) return le;
     time_end(c, 3);
     c->launches += 2;
     return cudaGetLastError();

@@ -296,8 +296,10 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
                     if (max(c0, max(c1, c2)) >= k - 1) {
                         ++my_faces;
                         float3 p[3];
+                        const float4 m = __ldg(&a.tm[j]);
+                        const float sd = __ldg(&a.tsd[j]);
                         int fv[3];
-                        face_vectors(a.xyz, tv, s, __ldg(&a.tm[j]), __ldg(&a.tsd[j]), p, fv);
+                        face_vectors(a.xyz, tv, s, m, sd, p, fv);
                         LocalRes r;
                         if (MODE == GBP_LOCAL_FISTA) {
                             const float4 Lq = __ldg(&a.tlip[j]);

@@ -206,10 +206,19 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
         float tp = f3dot(nrm, p[2]);
         float S = tp * tp / det;
         bool degenerate = !(det > 1e-6f * Q00 * Q11);
-        if (k < 1.f || degenerate) {
+        // The stationary point is x = x0 + w with x0 the foot of the
+        // perpendicular from the origin to the face plane (|x0|^2 = S) and
+        // |w|^2 = k S / (1 - k); inside the face requires |w| <= max_n |p_n|.
+        // When 1 - k is too small for FP32, that necessary condition (with
+        // a factor-2 and 1e-5 slack for the rounding of k) rules most faces
+        // out before the FP64 redo.
+        const float pmax2 = fmaxf(fmaxf(f3dot(p[0], p[0]), f3dot(p[1], p[1])), f3dot(p[2], p[2]));
+        const bool near_singular = 1.f - k < GBP_FP64_FALLBACK_TOL;
+        const bool outside = near_singular && k * S > 2.f * pmax2 * ((1.f - k) + 1e-5f);
+        if ((k < 1.f && !outside) || degenerate) {
             float b0, b1;
             bool found = false;
-            if (degenerate || 1.f - k < GBP_FP64_FALLBACK_TOL) {
+            if (degenerate || near_singular) {
                 ++*fb;
                 found = interior_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, ph[0],
                                       ph[1], ph[2], &b0, &b1);

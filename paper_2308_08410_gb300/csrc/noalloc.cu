@@ -14,8 +14,9 @@
 
 namespace gbp {
 // kernels shared with the context-based path (ecg.cu)
-__global__ void k_ecg_fwd(int64_t n_v, int N, int T, const float *__restrict__ L, const float *__restrict__ phi,
-                          float t0, float dt, float c4, int T_tile, int G, int64_t per_cta, float *__restrict__ part);
+cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
+                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
+                                 int64_t per, float *part);
 __global__ void k_ecg_reduce(int N, int T, int ncta, const float *__restrict__ part, const float *__restrict__ rowsum,
                              float K0, float dK, float *__restrict__ ecg);
 }  // namespace gbp
@@ -102,10 +103,9 @@ extern "C" gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t
     // every partial and row sum is overwritten below, so nothing is cleared
     k_rowsum_noalloc<<<N, 256, 0, st>>>(n_v, L, rowsum);
     size_t smem = sizeof(float) * (CH + (size_t)N * CH + (size_t)G * N * tt);
-    if (cudaFuncSetAttribute(gbp::k_ecg_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (gbp::launch_ecg_fwd_leads(N, (int)ncta, tt * G, smem, st, n_v, T, L, phi, tmpl->t0, tmpl->dt,
+                                  4.f / tmpl->tau, tt, G, per, part) != cudaSuccess)
         return GBP_ERR_CUDA;
-    gbp::k_ecg_fwd<<<(unsigned)ncta, tt * G, smem, st>>>(n_v, N, T, L, phi, tmpl->t0, tmpl->dt, 4.f / tmpl->tau, tt,
-                                                          G, per, part);
     gbp::k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, st>>>(N, T, (int)ncta, part, rowsum, tmpl->K0,
                                                           tmpl->K1 - tmpl->K0, ecg);
     return cudaGetLastError() == cudaSuccess ? GBP_OK : GBP_ERR_CUDA;
