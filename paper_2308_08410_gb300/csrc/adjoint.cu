@@ -15,14 +15,21 @@
 // mu = (I - P^T)^{-1} dL/dphi is accumulated children-first: a vertex is
 // processed once every child (vertex whose parent face holds it with
 // alpha > 0) has pushed alpha * mu into it.  This runs as a dataflow with no
-// grid barriers: the child whose decrement brings a parent's child count to
-// zero continues with that parent itself (further parents it readies go to a
-// work queue), so the critical path is the depth of the parent graph times
-// one vertex's latency.  The parent graph of the discrete fixed point can
-// hold short cycles (non-causal updates in anisotropic elements); the
-// vertices they block are finished by a bounded fixed-point (Jacobi)
-// iteration on the remaining sub-graph, which is closed under taking
-// parents.
+// grid barriers.  Each vertex owns one 64-bit word that packs its
+// outstanding child count (top 9 bits) and the fixed-point sum of the pushes
+// it has received (low 55 bits, two's complement, scale 2^e chosen from
+// sum |dL/dphi| so that every partial sum stays below 2^53): one atomic add
+// both delivers a child's contribution and decrements the count, and the
+// child that brings the count to zero receives the complete sum in the
+// atomic's return value.  No fence or re-read is needed on the chain, and
+// the sums are exact integers, so mu does not depend on the order of the
+// pushes.  That child continues with the parent itself; further parents it
+// readies go to a work queue of (vertex, mu) pairs.  The critical path is
+// the depth of the parent graph times one vertex's latency.  The parent
+// graph of the discrete fixed point can hold short cycles (non-causal
+// updates in anisotropic elements); the vertices they block are finished by
+// a bounded fixed-point (Jacobi) iteration on the remaining sub-graph, which
+// is closed under taking parents.
 #include "gbp_internal.cuh"
 
 namespace gbp {
@@ -38,8 +45,10 @@ struct AdjArgs {
     int onset_kind;
     const int *on_idx;
     const float *on_bary;
+    const float *lam;
     float *mu, *xj, *acc, *acc2;
-    int *cnt, *proc, *lists;
+    unsigned long long *w;  // packed (child count, fixed-point push sum) per vertex
+    int *proc, *lists;
     float *d_cf, *d_ct, *d_t, *d_x;
     Control *ctl;
     int max_cycle_iters;
@@ -121,18 +130,48 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int64_t i, int4 r,
     }
 }
 
-__global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const float *__restrict__ dphi, float *mu,
-                           int *cnt, int *proc, Control *ctl)
+// Packed per-vertex word: W = count * 2^55 + S with |S| < 2^54.
+constexpr int ADJ_CNT_SHIFT = 55;
+constexpr unsigned long long ADJ_ONE = 1ull << ADJ_CNT_SHIFT;
+constexpr int ADJ_MAX_CHILDREN = 511;
+
+__device__ __forceinline__ unsigned int adj_count(unsigned long long W)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_v) return;
-    bool reached = rec[i].x != GBP_UNREACHED;
-    mu[i] = reached ? dphi[i] : 0.f;
-    cnt[i] = 0;
-    proc[i] = reached ? 0 : 1;
+    return (unsigned int)((W + (1ull << (ADJ_CNT_SHIFT - 1))) >> ADJ_CNT_SHIFT);
 }
 
-__global__ void k_adj_count(int64_t n_v, const int4 *__restrict__ rec, const int4 *__restrict__ tets, int *cnt)
+__device__ __forceinline__ long long adj_sum(unsigned long long W)
+{
+    return (long long)(W - ((unsigned long long)adj_count(W) << ADJ_CNT_SHIFT));
+}
+
+__global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const float *__restrict__ dphi,
+                           unsigned long long *w, int *proc, Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool reached = i < n_v && rec[i].x != GBP_UNREACHED;
+    float l = reached ? fabsf(dphi[i]) : 0.f;
+    if (i < n_v) {
+        w[i] = 0ull;
+        proc[i] = reached ? 0 : 1;
+    }
+    // sum |dL/dphi| (bounds every push sum) for the fixed-point scale
+    __shared__ float red[32];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        l = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
+        // rounded up so that the sum stays an upper bound
+        if (threadIdx.x == 0 && l > 0.f) atomicAdd(&ctl->adj_lsum, 1.001 * (double)l);
+    }
+}
+
+__global__ void k_adj_count(int64_t n_v, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
+                            unsigned long long *w)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_v) return;
@@ -146,17 +185,23 @@ __global__ void k_adj_count(int64_t n_v, const int4 *__restrict__ rec, const int
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (q == s) continue;
-        if (__int_as_float(al[q3]) != 0.f) atomicAdd(&cnt[ids[q]], 1);
+        if (__int_as_float(al[q3]) != 0.f) atomicAdd(&w[ids[q]], ADJ_ONE);
         ++q3;
     }
 }
 
+// queue slot: vertex id (low word) and mu bits (high word); empty = all ones
+__device__ __forceinline__ unsigned long long adj_item(int v, float m)
+{
+    return (unsigned long long)(unsigned int)v | ((unsigned long long)__float_as_uint(m) << 32);
+}
+
 // vertices with no children start the dataflow: they go to the work queue
-__global__ void k_adj_seed(int64_t n_v, const int *__restrict__ cnt, const int *__restrict__ proc, int *queue,
-                           Control *ctl)
+__global__ void k_adj_seed(int64_t n_v, const unsigned long long *__restrict__ w, const int *__restrict__ proc,
+                           const float *__restrict__ dphi, unsigned long long *queue, Control *ctl)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool app = i < n_v && proc[i] == 0 && cnt[i] == 0;
+    bool app = i < n_v && proc[i] == 0 && w[i] == 0ull;
     unsigned int mask = __ballot_sync(0xffffffffu, app);
     if (mask == 0) return;
     const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
@@ -167,7 +212,14 @@ __global__ void k_adj_seed(int64_t n_v, const int *__restrict__ cnt, const int *
         atomicAdd(&ctl->adj_levels, __popc(mask));  // number of seeds, reported in the stats
     }
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (app) queue[base + __popc(mask & ((1u << lane) - 1u))] = (int)i;
+    if (app) queue[base + __popc(mask & ((1u << lane) - 1u))] = adj_item((int)i, dphi[i]);
+}
+
+// A vertex has more children than the packed count holds.
+__global__ void k_adj_check(int64_t n_v, const unsigned long long *__restrict__ w, Control *ctl)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_v && adj_count(w[i]) > (unsigned)ADJ_MAX_CHILDREN) atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
 }
 
 __device__ __forceinline__ float ld_cg_f(const float *p) { return __ldcg(p); }
@@ -197,26 +249,30 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     int mine = 0;
     if (tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[0]));
     // ---- dataflow phase (no grid barrier per level) ----
-    // The vertices readied so far sit in a work queue (lists[0..n_v), slots
-    // start at -1).  Every thread takes tickets; the holder of ticket h
-    // processes the vertex in slot h, then continues itself with the first
-    // parent it readies (the child that brings a parent's count to zero) and
+    // The vertices readied so far sit in a work queue of (vertex, mu) items
+    // (lists[0..2 n_v) as n_v 64-bit slots, empty = all ones).  Every
+    // thread takes tickets; the holder of ticket h processes the item in
+    // slot h, then continues itself with the first parent it readies and
     // queues any further ones.  q_active counts queued items plus chains in
     // progress; it reaches zero only when no more work can appear.
-    int *queue = a.lists;
+    const double lsum = ld_relaxed_f64(&a.ctl->adj_lsum);
+    // power-of-two scale with sum |dL/dphi| * scale <= 2^53
+    const int ex = lsum > 0.0 ? ilogb(lsum) + 1 : 0;
+    const double scale = ldexp(1.0, 53 - ex), iscale = ldexp(1.0, ex - 53);
+    unsigned long long *queue = reinterpret_cast<unsigned long long *>(a.lists);
     for (;;) {
         const int h = atomicAdd(&a.ctl->q_head, 1);
-        int v = -1;
+        unsigned long long item = ~0ull;
         unsigned int spins = 0, sleep_ns = 32;
         for (;;) {
             if (h < n_v) {
-                v = ld_acquire_i32(&queue[h]);
-                if (v >= 0) break;
+                item = ld_relaxed_u64(&queue[h]);
+                if (item != ~0ull) break;
             }
             if ((spins & 15) == 0) {
                 if (ld_acquire_i32(&a.ctl->q_active) == 0) {
                     // the last push (if any) happened before the count reached zero
-                    if (h < n_v) v = ld_acquire_i32(&queue[h]);
+                    if (h < n_v) item = ld_relaxed_u64(&queue[h]);
                     break;
                 }
                 if (ld_relaxed_i32(&a.ctl->abort)) break;
@@ -230,43 +286,51 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             __nanosleep(sleep_ns);
             if (sleep_ns < 1024) sleep_ns <<= 1;
         }
-        if (v < 0) break;
+        if (item == ~0ull) break;
+        int v = (int)(unsigned int)(item & 0xffffffffu);
+        float m = __uint_as_float((unsigned int)(item >> 32));
         while (v >= 0) {
-            const float m = ld_cg_f(&a.mu[v]);
             const int4 r = __ldg(&a.rec[v]);
+            a.mu[v] = m;
             a.proc[v] = 1;
             ++mine;
-            local_terms(a, v, r, m);
             int next = -1;
+            float mnext = 0.f;
             if (r.x >= 0) {
                 const int j = r.x >> 2, s = r.x & 3;
                 const int4 tv = __ldg(&a.tets[j]);
                 const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
                 const int f[3] = {s == 0 ? tv.y : tv.x, s <= 1 ? tv.z : tv.y, s <= 2 ? tv.w : tv.z};
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (al[q] != 0.f) atomicAdd(&a.mu[f[q]], al[q] * m);
-                // the pushes land before the counts they release
-                __threadfence();
-                int left[3] = {1, 1, 1};
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    if (al[q] != 0.f) left[q] = atomicSub(&a.cnt[f[q]], 1);
+                unsigned long long nw[3] = {0ull, 0ull, 0ull};
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    if (al[q] == 0.f || left[q] != 1) continue;
+                    if (al[q] == 0.f) continue;
+                    const long long c = __double2ll_rn((double)(al[q] * m) * scale);
+                    const unsigned long long d = (unsigned long long)c - ADJ_ONE;
+                    nw[q] = atomicAdd(&a.w[f[q]], d) + d;
+                }
+                local_terms(a, v, r, m);
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if (al[q] == 0.f || adj_count(nw[q]) != 0u) continue;
+                    // this push completed f[q]: its mu is lambda plus the whole sum
+                    const float mp = __ldg(&a.lam[f[q]]) + (float)((double)adj_sum(nw[q]) * iscale);
                     if (next < 0) {
                         next = f[q];
+                        mnext = mp;
                     } else {
                         atomicAdd(&a.ctl->q_active, 1);
                         const int pos = atomicAdd(&a.ctl->q_res, 1);
-                        st_release_i32(&queue[pos], f[q]);
+                        st_relaxed_u64(&queue[pos], adj_item(f[q], mp));
                     }
                 }
+            } else {
+                local_terms(a, v, r, m);
             }
             v = next;
-            if (v >= 0) __threadfence();
+            m = mnext;
         }
+        // this chain's queue pushes are counted before it leaves
         __threadfence();
         atomicSub(&a.ctl->q_active, 1);
     }
@@ -282,12 +346,15 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     // ---- vertices blocked by cycles: fixed-point iteration ----
     // collect the unprocessed reached vertices R (closed under parents); the
     // barrier above ordered every write of the dataflow phase before this
-    int *R = a.lists + n_v;
+    int *R = a.lists + 2 * n_v;
     for (int64_t base = 0; base < n_v; base += nth) {
         const int64_t i = base + tid;
         bool app = i < n_v && __ldcg(&a.proc[i]) == 0;
         if (app) {
-            a.xj[i] = ld_cg_f(&a.mu[i]);
+            // base value: lambda plus the pushes of the processed children
+            const float b0 = __ldg(&a.lam[i]) + (float)((double)adj_sum(__ldcg(&a.w[i])) * iscale);
+            a.mu[i] = b0;
+            a.xj[i] = b0;
             a.acc[i] = 0.f;
             a.acc2[i] = 0.f;
         }
@@ -393,9 +460,10 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->q_active, 0, sizeof(int), c->stream);
     if (err) return err;
-    err = cudaMemsetAsync(c->lists, 0xff, sizeof(int) * n_v, c->stream);  // empty queue slots
+    err = cudaMemsetAsync(c->lists, 0xff, sizeof(unsigned long long) * n_v, c->stream);  // empty queue slots
     if (err) return err;
-    err = cudaMemsetAsync(&c->ctl->adj_levels, 0, sizeof(int) * 4 + 6 * sizeof(float), c->stream);
+    err = cudaMemsetAsync(&c->ctl->adj_levels, 0, offsetof(Control, adj_ts) - offsetof(Control, adj_levels),
+                          c->stream);
     if (err) return err;
     if (d_cf) cudaMemsetAsync(d_cf, 0, sizeof(float) * c->n_t, c->stream);
     if (d_ct) cudaMemsetAsync(d_ct, 0, sizeof(float) * c->n_t, c->stream);
@@ -404,9 +472,14 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     int th = 256;
     unsigned bl = (unsigned)((n_v + th - 1) / th);
     time_begin(c, 4);
-    k_adj_init<<<bl, th, 0, c->stream>>>(n_v, c->rec, dphi, c->mu, c->cnt, c->proc, c->ctl);
-    k_adj_count<<<bl, th, 0, c->stream>>>(n_v, c->rec, c->tets, c->cnt);
-    k_adj_seed<<<bl, th, 0, c->stream>>>(n_v, c->cnt, c->proc, c->lists, c->ctl);
+    k_adj_init<<<bl, th, 0, c->stream>>>(n_v, c->rec, dphi, c->adj_w, c->proc, c->ctl);
+    k_adj_count<<<bl, th, 0, c->stream>>>(n_v, c->rec, c->tets, c->adj_w);
+    if (c->max_nbr > ADJ_MAX_CHILDREN) {
+        k_adj_check<<<bl, th, 0, c->stream>>>(n_v, c->adj_w, c->ctl);
+        c->launches++;
+    }
+    k_adj_seed<<<bl, th, 0, c->stream>>>(n_v, c->adj_w, c->proc, dphi,
+                                         reinterpret_cast<unsigned long long *>(c->lists), c->ctl);
     c->launches += 3;
     if ((err = cudaGetLastError())) return err;
     AdjArgs a;
@@ -421,11 +494,12 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.onset_kind = c->onset_kind;
     a.on_idx = c->on_idx;
     a.on_bary = c->on_bary;
+    a.lam = dphi;
     a.mu = c->mu;
+    a.w = c->adj_w;
     a.xj = c->jac_x;
     a.acc = c->jac_acc;
     a.acc2 = c->jac_acc2;
-    a.cnt = c->cnt;
     a.proc = c->proc;
     a.lists = c->lists;
     a.d_cf = d_cf;

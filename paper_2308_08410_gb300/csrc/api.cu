@@ -74,7 +74,7 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->jac_x);
     dfree(&c->jac_acc);
     dfree(&c->jac_acc2);
-    dfree(&c->cnt);
+    dfree(&c->adj_w);
     dfree(&c->proc);
     dfree(&c->L);
     dfree(&c->Lbf);
@@ -278,7 +278,7 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
         for (int64_t j = 0; j < n_t; ++j)
             for (int q = 0; q < 4; ++q) n2t[cur[tets[4 * j + q]]++] = (int)(4 * j + q);
     }
-    int max_deg = 0;
+    int max_deg = 0, max_nbr = 0;
     // vertex -> vertex (neighbours through a shared tet)
     std::vector<int> n2n_ptr(n_v + 1, 0), n2n;
     n2n.reserve((size_t)n_t * 3);
@@ -297,12 +297,14 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
         std::sort(buf.begin(), buf.end());
         buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
         n2n.insert(n2n.end(), buf.begin(), buf.end());
+        max_nbr = std::max(max_nbr, (int)buf.size());
         n2n_ptr[i + 1] = (int)n2n.size();
     }
     free_mesh_buffers(c);
     c->n_v = n_v;
     c->n_t = n_t;
     c->max_deg = max_deg;
+    c->max_nbr = max_nbr;
     std::vector<float4> x4(n_v);
     for (int64_t i = 0; i < n_v; ++i) x4[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
     cudaError_t err = cudaSuccess;
@@ -332,7 +334,7 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     CK(dalloc(&c->jac_x, n_v));
     CK(dalloc(&c->jac_acc, n_v));
     CK(dalloc(&c->jac_acc2, n_v));
-    CK(dalloc(&c->cnt, n_v));
+    CK(dalloc(&c->adj_w, n_v));
     CK(dalloc(&c->proc, n_v));
     CK(dalloc(&c->dphi, n_v));
     CK(cudaMemcpy(c->xyz, x4.data(), sizeof(float4) * n_v, cudaMemcpyHostToDevice));

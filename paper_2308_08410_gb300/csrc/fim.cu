@@ -220,6 +220,9 @@ struct FimArgs {
 #ifndef GBP_FIM_G
 #define GBP_FIM_G 8  // lanes per active vertex
 #endif
+#ifndef GBP_FIM_DYN
+#define GBP_FIM_DYN 0  // warps fetch active vertices from a counter (else a fixed stride)
+#endif
 #ifndef GBP_FIM_BLOCK
 #define GBP_FIM_BLOCK 256  // threads per CTA
 #endif
@@ -265,13 +268,24 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
         if (n_cand == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.ctl->count[nn] = 0;
+            a.ctl->fim_fetch[nxt] = 0;  // last used at k-2, next used at k+1
             s_cand += (unsigned long long)n_cand;
         }
         const int *list = a.lists + (int64_t)cur * n_v;
         int *nlist = a.lists + (int64_t)nxt * n_v;
+#if GBP_FIM_DYN
+        for (;;) {
+            int wbase = 0;
+            if (lane == 0) wbase = atomicAdd(&a.ctl->fim_fetch[cur], 32 / FIM_G);
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            if (wbase >= n_cand) break;
+            const int64_t g = wbase + lane / FIM_G;
+            const bool act = g < n_cand;
+#else
         for (int64_t g = ggroup;; g += ngroups) {
             const bool act = g < n_cand;
             if (!__any_sync(0xffffffffu, act)) break;
+#endif
             int i = 0, beg = 0, end = 0;
             float phi_old = 0.f;
             if (act) {

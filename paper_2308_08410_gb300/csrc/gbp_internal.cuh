@@ -42,12 +42,15 @@ struct Control {
     int padq1[31];
     int q_active;                 // chains queued or in progress
     int padq2[31];
+    int fim_fetch[3];             // FIM work counters (rotating with the active lists)
+    int padq3[29];
     int adj_levels;
     int adj_cycle_nodes;
     int adj_cycle_iters;
     int adj_processed;
     float adj_delta[3];           // max |dx| of the cycle iteration (rotating slots)
     float adj_xmax[3];            // max |x| of the cycle iteration (rotating slots)
+    double adj_lsum;              // sum |dL/dphi| (scale of the adjoint's fixed-point sums)
     unsigned long long adj_ts[3]; // global timer at adjoint start, end of dataflow, end
     int pad[3];
     int param_status;             // latched by the metric precompute (kept across solves)
@@ -368,6 +371,25 @@ __device__ __forceinline__ int ld_relaxed_i32(const int *p)
     return v;
 }
 
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ double ld_relaxed_f64(const double *p)
+{
+    double v;
+    asm volatile("ld.relaxed.gpu.global.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -469,7 +491,9 @@ struct gbp_ctx {
     int64_t param_gen = 0, solve_gen = -1;
     // adjoint state
     float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;
-    int *cnt = nullptr, *proc = nullptr;
+    unsigned long long *adj_w = nullptr;  // adjoint: packed (child count, push sum) per vertex
+    int *proc = nullptr;
+    int max_nbr = 0;  // longest vertex->vertex row (bounds a vertex's child count)
     // ECG scratch
     float *ecg_part = nullptr;
     int64_t ecg_part_cap = 0;

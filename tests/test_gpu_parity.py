@@ -73,6 +73,43 @@ def test_local_exact(ctx, skinny):
     assert np.median(np.abs(a - a_ref).max(axis=1)) < 1e-4
 
 
+def near_singular_faces(n, seed):
+    """Isotropic faces (c_f = c_t = 1, so the metric is the identity) whose
+    vertex values are a linear function with in-plane slope sqrt(1 - delta),
+    delta ~ 10^U(-8, -2): the interior stationary point's denominator 1 - k is
+    tiny, the case the FP32 solver hands to the FP64 step or rules out by the
+    infeasibility test.  A third of the faces are nearly flat (v_i close to
+    the face plane), which keeps some of those stationary points inside."""
+    rng = np.random.default_rng(seed)
+    e = rng.standard_normal((n, 3, 3))
+    flat = rng.random(n) < 0.33
+    nrm = np.cross(e[:, 0] - e[:, 2], e[:, 1] - e[:, 2])
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    h = np.einsum("nr,nr->n", nrm, e[:, 2])
+    e[flat] -= ((1 - 10 ** rng.uniform(-3, -1, flat.sum())) * h[flat])[:, None, None] * nrm[flat][:, None, :]
+    d1 = e[:, 0] - e[:, 2]
+    d2 = e[:, 1] - e[:, 2]
+    w = rng.standard_normal((n, 2))
+    u = w[:, :1] * d1 + w[:, 1:] * d2
+    u /= np.linalg.norm(u, axis=1, keepdims=True)
+    s = np.sqrt(1 - 10 ** rng.uniform(-8, -2, n))
+    phi = 5.0 + s[:, None] * np.einsum("nr,nkr->nk", u, e)
+    f = rng.standard_normal((n, 3))
+    f /= np.linalg.norm(f, axis=1, keepdims=True)
+    one = np.ones(n)
+    return (e.astype(np.float32), f.astype(np.float32), one.astype(np.float32), one.astype(np.float32),
+            phi.astype(np.float32))
+
+
+def test_local_exact_near_singular(ctx):
+    e, f, cf, ct, phi = near_singular_faces(50000, seed=11)
+    v_ref, _ = O.local_batch(e, f, cf, ct, phi)
+    v, _ = ctx.local_solve_batch(dev(e), dev(f), dev(cf), dev(ct), dev(phi))
+    v = v.cpu().numpy().astype(float)
+    rel = np.abs(v - v_ref) / np.maximum(1.0, np.abs(v_ref))
+    assert rel.max() < 2e-6, rel.max()
+
+
 def test_local_fista(ctx):
     e, f, cf, ct, phi = S.random_faces(20000, seed=5, p_inf=0.15)
     v_ref, _ = O.local_batch(e, f, cf, ct, phi, mode=O.FISTA, n_f=32)
