@@ -250,46 +250,54 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     if (tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[0]));
     // ---- dataflow phase (no grid barrier per level) ----
     // The vertices readied so far sit in a work queue of (vertex, mu) items
-    // (lists[0..2 n_v) as n_v 64-bit slots, empty = all ones).  Every
-    // thread takes tickets; the holder of ticket h processes the item in
-    // slot h, then continues itself with the first parent it readies and
-    // queues any further ones.  q_active counts queued items plus chains in
-    // progress; it reaches zero only when no more work can appear.
+    // (lists[0..2 n_v) as n_v 64-bit slots, empty = all ones); q_res counts
+    // the slots produced, q_head the slots handed out, and q_active the
+    // queued items plus chains in progress (it reaches zero only when no
+    // more work can appear).  Each warp runs up to 32 chains in lockstep:
+    // every pass, idle lanes take the items that are available (one atomic
+    // per warp), then every busy lane processes one vertex and moves on to
+    // the first parent it readied, queueing any further ones.  A warp sleeps
+    // only when none of its lanes has work.
     const double lsum = ld_relaxed_f64(&a.ctl->adj_lsum);
     // power-of-two scale with sum |dL/dphi| * scale <= 2^53
     const int ex = lsum > 0.0 ? ilogb(lsum) + 1 : 0;
     const double scale = ldexp(1.0, 53 - ex), iscale = ldexp(1.0, ex - 53);
     unsigned long long *queue = reinterpret_cast<unsigned long long *>(a.lists);
+    const int lane = threadIdx.x & 31;
+    int v = -1;        // vertex this lane is processing
+    float m = 0.f;     // its mu
+    int pending = -1;  // a slot handed to this lane that was still empty
+    unsigned int idle_spins = 0, sleep_ns = 32;
     for (;;) {
-        const int h = atomicAdd(&a.ctl->q_head, 1);
-        unsigned long long item = ~0ull;
-        unsigned int spins = 0, sleep_ns = 32;
-        for (;;) {
-            if (h < n_v) {
-                item = ld_relaxed_u64(&queue[h]);
-                if (item != ~0ull) break;
+        // hand available slots to the idle lanes
+        const unsigned int idle = __ballot_sync(0xffffffffu, v < 0 && pending < 0);
+        if (idle) {
+            int base = 0, got = 0;
+            if (lane == 0) {
+                const int avail = ld_relaxed_i32(&a.ctl->q_res) - ld_relaxed_i32(&a.ctl->q_head);
+                got = min(__popc(idle), avail);
+                if (got > 0) base = atomicAdd(&a.ctl->q_head, got);
             }
-            if ((spins & 15) == 0) {
-                if (ld_acquire_i32(&a.ctl->q_active) == 0) {
-                    // the last push (if any) happened before the count reached zero
-                    if (h < n_v) item = ld_relaxed_u64(&queue[h]);
-                    break;
-                }
-                if (ld_relaxed_i32(&a.ctl->abort)) break;
-            }
-            if (++spins > (1u << 21)) {
-                atomicExch(&a.ctl->abort, 1);
-                atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_TIMEOUT);
-                ok = false;
-                break;
-            }
-            __nanosleep(sleep_ns);
-            if (sleep_ns < 1024) sleep_ns <<= 1;
+            got = __shfl_sync(0xffffffffu, got, 0);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const int rank = __popc(idle & ((1u << lane) - 1u));
+            if (((idle >> lane) & 1u) && rank < got) pending = base + rank;
         }
-        if (item == ~0ull) break;
-        int v = (int)(unsigned int)(item & 0xffffffffu);
-        float m = __uint_as_float((unsigned int)(item >> 32));
-        while (v >= 0) {
+        // a slot handed out may still be empty if other warps took the items
+        // counted as available; it fills once its producer stores it
+        if (pending >= 0) {
+            const unsigned long long item = pending < n_v ? ld_relaxed_u64(&queue[pending]) : 0ull;
+            if (pending >= n_v) {
+                pending = -1;  // cannot happen: at most n_v items are ever queued
+            } else if (item != ~0ull) {
+                v = (int)(unsigned int)(item & 0xffffffffu);
+                m = __uint_as_float((unsigned int)(item >> 32));
+                pending = -1;
+            }
+        }
+        // one vertex per busy lane
+        int ended = 0;
+        if (v >= 0) {
             const int4 r = __ldg(&a.rec[v]);
             a.mu[v] = m;
             a.proc[v] = 1;
@@ -329,10 +337,53 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             }
             v = next;
             m = mnext;
+            ended = v < 0;
         }
-        // this chain's queue pushes are counted before it leaves
-        __threadfence();
-        atomicSub(&a.ctl->q_active, 1);
+        // retire the chains that ended: their pushes are counted first
+        const unsigned int ends = __ballot_sync(0xffffffffu, ended);
+        if (ends) {
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                atomicSub(&a.ctl->q_active, __popc(ends));
+            }
+        }
+        if (__ballot_sync(0xffffffffu, v >= 0)) {
+            idle_spins = 0;
+            sleep_ns = 32;
+            continue;
+        }
+        // no lane is processing: finished when no work can appear any more
+        int done = 0;
+        if (lane == 0) {
+            done = ld_acquire_i32(&a.ctl->q_active) == 0;
+            if (!done && ld_relaxed_i32(&a.ctl->abort)) done = 2;
+        }
+        done = __shfl_sync(0xffffffffu, done, 0);
+        if (done == 2) break;
+        if (done) {
+            // a pending slot can only have been filled before the count reached zero
+            if (pending >= 0) {
+                const unsigned long long item = ld_relaxed_u64(&queue[pending]);
+                pending = -1;
+                if (item != ~0ull) {
+                    v = (int)(unsigned int)(item & 0xffffffffu);
+                    m = __uint_as_float((unsigned int)(item >> 32));
+                }
+            }
+            if (!__ballot_sync(0xffffffffu, v >= 0)) break;
+            continue;
+        }
+        if (++idle_spins > (1u << 21)) {
+            if (lane == 0) {
+                atomicExch(&a.ctl->abort, 1);
+                atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_TIMEOUT);
+            }
+            ok = false;
+            break;
+        }
+        __nanosleep(sleep_ns);
+        if (sleep_ns < 512) sleep_ns <<= 1;
     }
     if (mine) atomicAdd(&s_proc, mine);
     __syncthreads();

@@ -94,18 +94,6 @@ cudaError_t launch_lipschitz(gbp_ctx *c)
 // ---------------------------------------------------------------------------
 // onset seeding (Algorithm 2 initialisation, Eq. upwind_xi)
 // ---------------------------------------------------------------------------
-// Order-preserving map of a float onto an unsigned key, so that the smallest
-// value (ties: smallest onset index) wins an atomicMin.
-__device__ __forceinline__ unsigned int float_key(float v)
-{
-    unsigned int b = __float_as_uint(v);
-    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float key_float(unsigned int k)
-{
-    unsigned int b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
-    return __uint_as_float(b);
-}
 
 __global__ void k_onset_keys(int K, int kind, const int *__restrict__ idx, const float *__restrict__ bary,
                              const float *__restrict__ t, int64_t n_v, int64_t n_t, const float4 *__restrict__ xyz,
@@ -432,8 +420,24 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
                                                               c->ctl);
     unsigned bl = (unsigned)((n_v + th - 1) / th);
     k_init_nodes<<<bl, th, 0, c->stream>>>(n_v, c->keys, c->phi, c->rec, c->chg, c->stamp);
+    c->launches += 2;
+    if ((err = cudaGetLastError())) return err;
+    long long *trace = nullptr;
+    if (c->trace_on) {
+        if (c->trace_cap < o->max_iters + 2) {
+            if (c->trace) cudaFree(c->trace);
+            c->trace = nullptr;
+            c->trace_cap = 0;
+            if (cudaMalloc(&c->trace, sizeof(long long) * 2 * (o->max_iters + 2)) == cudaSuccess)
+                c->trace_cap = o->max_iters + 2;
+        }
+        if (c->trace) {
+            cudaMemsetAsync(c->trace, 0, sizeof(long long) * 2 * c->trace_cap, c->stream);
+            trace = c->trace;
+        }
+    }
     k_seed_lists<<<bl, th, 0, c->stream>>>(n_v, c->keys, c->n2n_ptr, c->n2n, c->stamp, c->lists + n_v, c->ctl);
-    c->launches += 3;
+    c->launches++;
     if ((err = cudaGetLastError())) return err;
 
     FimArgs a;
@@ -456,20 +460,7 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     a.eps = o->eps;
     a.max_iters = o->max_iters;
     a.n_f = o->n_f;
-    a.trace = nullptr;
-    if (c->trace_on) {
-        if (c->trace_cap < o->max_iters + 2) {
-            if (c->trace) cudaFree(c->trace);
-            c->trace = nullptr;
-            c->trace_cap = 0;
-            if (cudaMalloc(&c->trace, sizeof(long long) * 2 * (o->max_iters + 2)) == cudaSuccess)
-                c->trace_cap = o->max_iters + 2;
-        }
-        if (c->trace) {
-            cudaMemsetAsync(c->trace, 0, sizeof(long long) * 2 * c->trace_cap, c->stream);
-            a.trace = c->trace;
-        }
-    }
+    a.trace = trace;
     const void *fn = o->local_solver == GBP_LOCAL_FISTA ? (const void *)k_fim<GBP_LOCAL_FISTA>
                                                         : (const void *)k_fim<GBP_LOCAL_EXACT>;
     int grid = fim_grid(c, fn);

@@ -78,6 +78,19 @@ __device__ __forceinline__ float3 f3cross(float3 a, float3 b)
 }
 __device__ __forceinline__ float3 f4to3(float4 a) { return make_float3(a.x, a.y, a.z); }
 
+// Order-preserving map of a float onto an unsigned key, so that the smallest
+// value (ties: the smaller low word of a packed 64-bit key) wins an atomicMin.
+__device__ __forceinline__ unsigned int float_key(float v)
+{
+    unsigned int b = __float_as_uint(v);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(unsigned int k)
+{
+    unsigned int b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    return __uint_as_float(b);
+}
+
 struct LocalRes {
     float v;
     float a0, a1, a2;
@@ -156,12 +169,15 @@ static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0
 #endif
 
 // Exact minimiser of Eq. (upwind_eq_lsqr) on one face (Sec. II-B).  The
-// objective is convex on the simplex, so the minimum is at a KKT point:
-// the stationary point of the face interior, of an edge, or a vertex.  All
-// feasible candidates are evaluated at their (feasible) point and the
-// smallest value wins; vertices first, then edges, then the interior, ties
-// to the earlier one.  p[n] = R (v_{j_n} - v_i), ph[n] = Phi_n (+inf allowed).
-// fb counts FP64 fallbacks.
+// objective is convex on the simplex, so the minimum is at a KKT point: the
+// stationary point of the face interior, of an edge, or a vertex.  A
+// feasible interior stationary point is the minimiser, so it is tried first
+// and ends the search; otherwise all feasible edge and vertex candidates are
+// evaluated at their (feasible) point and the smallest value wins, vertices
+// first, then edges, ties to the earlier one.  Locations (lambda, beta) use
+// approximate reciprocals (a location error only costs second order in the
+// value); values use IEEE square roots.  p[n] = R (v_{j_n} - v_i),
+// ph[n] = Phi_n (+inf allowed).  fb counts FP64 fallbacks.
 __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float ph[3], int *fb)
 {
     LocalRes r;
@@ -170,45 +186,19 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
     bool ok0 = ph[0] < GBP_INF, ok1 = ph[1] < GBP_INF, ok2 = ph[2] < GBP_INF;
     if (!(ok0 || ok1 || ok2)) return r;
     float ref = fminf(fminf(ok0 ? ph[0] : GBP_INF, ok1 ? ph[1] : GBP_INF), ok2 ? ph[2] : GBP_INF);
-    // vertices
-    if (ok0) GBP_TRY(1.f, 0.f, 0.f);
-    if (ok1) GBP_TRY(0.f, 1.f, 0.f);
-    if (ok2) GBP_TRY(0.f, 0.f, 1.f);
-    // edges (n, m), lambda = weight on n
-#pragma unroll
-    for (int e = 0; e < 3; ++e) {
-        const int n = e == 2 ? 1 : 0;
-        const int m = e == 0 ? 1 : 2;
-        bool okn = n == 0 ? ok0 : ok1;
-        bool okm = m == 1 ? ok1 : ok2;
-        if (!(okn && okm)) continue;
-        float3 u = f3sub(p[n], p[m]);
-        float A = f3dot(u, u);
-        float dl = ph[n] - ph[m];
-        float g = dl * dl / A;
-        if (!(g < 1.f)) continue;
-        float3 cr = f3cross(u, p[m]);
-        float S = f3dot(cr, cr) / A;
-        float h = sqrtf(S / (1.f - g));
-        float lam = (-dl * h - f3dot(u, p[m])) / A;
-        if (!(lam > 0.f && lam < 1.f)) continue;
-        float an = lam, am = 1.f - lam;
-        if (e == 0) GBP_TRY(an, am, 0.f);
-        else if (e == 1) GBP_TRY(an, 0.f, am);
-        else GBP_TRY(0.f, an, am);
-    }
     // interior
     if (ok0 && ok1 && ok2) {
         float3 d1 = f3sub(p[0], p[2]), d2 = f3sub(p[1], p[2]);
         float Q00 = f3dot(d1, d1), Q01 = f3dot(d1, d2), Q11 = f3dot(d2, d2);
         float3 nrm = f3cross(d1, d2);
         float det = f3dot(nrm, nrm);
+        bool degenerate = !(det > 1e-6f * Q00 * Q11);
+        float idet = __fdividef(1.f, det);
         float q0 = f3dot(d1, p[2]), q1 = f3dot(d2, p[2]);
         float D0 = ph[0] - ph[2], D1 = ph[1] - ph[2];
-        float k = (Q11 * D0 * D0 - 2.f * Q01 * D0 * D1 + Q00 * D1 * D1) / det;
+        float k = (Q11 * D0 * D0 - 2.f * Q01 * D0 * D1 + Q00 * D1 * D1) * idet;
         float tp = f3dot(nrm, p[2]);
-        float S = tp * tp / det;
-        bool degenerate = !(det > 1e-6f * Q00 * Q11);
+        float S = tp * tp * idet;
         // The stationary point is x = x0 + w with x0 the foot of the
         // perpendicular from the origin to the face plane (|x0|^2 = S) and
         // |w|^2 = k S / (1 - k); inside the face requires |w| <= max_n |p_n|.
@@ -226,14 +216,45 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
                 found = interior_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, ph[0],
                                       ph[1], ph[2], &b0, &b1);
             } else {
-                float h = sqrtf(S / (1.f - k));
+                float h = sqrtf(S * __fdividef(1.f, 1.f - k));
                 float y0 = fmaf(h, D0, q0), y1 = fmaf(h, D1, q1);
-                b0 = -(Q11 * y0 - Q01 * y1) / det;
-                b1 = -(Q00 * y1 - Q01 * y0) / det;
+                b0 = -(Q11 * y0 - Q01 * y1) * idet;
+                b1 = -(Q00 * y1 - Q01 * y0) * idet;
                 found = b0 > 0.f && b1 > 0.f && b0 + b1 < 1.f;
             }
-            if (found) GBP_TRY(b0, b1, 1.f - b0 - b1);
+            if (found) {
+                GBP_TRY(b0, b1, 1.f - b0 - b1);
+                return r;
+            }
         }
+    }
+    // vertices
+    if (ok0) GBP_TRY(1.f, 0.f, 0.f);
+    if (ok1) GBP_TRY(0.f, 1.f, 0.f);
+    if (ok2) GBP_TRY(0.f, 0.f, 1.f);
+    // edges (n, m), lambda = weight on n
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int n = e == 2 ? 1 : 0;
+        const int m = e == 0 ? 1 : 2;
+        bool okn = n == 0 ? ok0 : ok1;
+        bool okm = m == 1 ? ok1 : ok2;
+        if (!(okn && okm)) continue;
+        float3 u = f3sub(p[n], p[m]);
+        float A = f3dot(u, u);
+        float iA = __fdividef(1.f, A);
+        float dl = ph[n] - ph[m];
+        float g = dl * dl * iA;
+        if (!(g < 1.f)) continue;
+        float3 cr = f3cross(u, p[m]);
+        float S = f3dot(cr, cr) * iA;
+        float h = sqrtf(S * __fdividef(1.f, 1.f - g));
+        float lam = (-dl * h - f3dot(u, p[m])) * iA;
+        if (!(lam > 0.f && lam < 1.f)) continue;
+        float an = lam, am = 1.f - lam;
+        if (e == 0) GBP_TRY(an, am, 0.f);
+        else if (e == 1) GBP_TRY(an, 0.f, am);
+        else GBP_TRY(0.f, an, am);
     }
     return r;
 }
