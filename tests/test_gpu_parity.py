@@ -237,6 +237,22 @@ def test_gradient_generic(ctx, kind):
         assert np.all(g["d_x"] == 0)
 
 
+def test_gradient_vs_unrolled_autograd(ctx):
+    """The CUDA frozen-graph adjoint against automatic differentiation
+    through the unrolled Jacobi iterations of Algorithm 2 (the paper's way,
+    oracle/unrolled.py) on a jittered 8^3 cube with element onsets."""
+    from oracle import unrolled as UR
+    p = jittered_c1(n=8, seed=4)
+    dp = gbp.setup_problem(ctx, p)
+    out = ctx.forward_backward(dp.cf, dp.ct, dev(p.extra["target"]), p.tmpl)
+    assert ctx.stats()["status"] == 0
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    u = UR.gradients(p.mesh, p.fib, p.cf, p.ct, p.onsets, p.L, p.tmpl, p.extra["target"])
+    assert abs(g["loss"][0] - u["loss"]) / u["loss"] < 1e-4
+    for k in ("d_cf", "d_ct", "d_t", "d_x"):
+        assert rel_l2(g[k], u[k]) < 1e-3, (k, rel_l2(g[k], u[k]))
+
+
 def test_gradient_c1_plain(ctx):
     """Plain c1: tets of one depth share a metric, so edge/vertex minimisers
     tie between tets and the per-tet velocity gradient is not unique there.
