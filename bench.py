@@ -3,11 +3,14 @@
 tet-updates per second on the 72^3 Kuhn cube (373,248 vertices,
 2,147,466 tets), FP32 eikonal / ECG / adjoint on one GB300 per rank.
 
-One step = one forward-plus-gradient evaluation through the C ABI
-(gbp_forward_backward): per-tet metric precompute, onset seeding, the
-persistent FIM eikonal solve with parent record, the parent pass, the
-lead-field ECG (8 leads x 150 samples), the misfit and its phi-derivative,
-and the frozen-graph adjoint to per-tet c_f, c_t, onset times and positions.
+One step = a batch of B forward-plus-gradient evaluations through the C ABI
+(gbp_forward_backward_batch; B = 8 starts of the inverse problem by
+default, gbp_forward_backward when B = 1): per-tet metric precompute, onset
+seeding, the persistent FIM eikonal solve with parent record, the parent
+pass, the lead-field ECG (8 leads x 150 samples), the misfit and its
+phi-derivative, and the frozen-graph adjoint to per-tet c_f, c_t, onset
+times and positions.  value = evaluations / second; the same line also
+reports one evaluation per step ("single").
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbp|reference]
 
@@ -32,6 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Geodesic-BP fwd+grad evals/s at 2.15M tets (72^3 Kuhn cube, FP32)"
+BATCH = 8                     # default problems per step (multi-start batch)
 BYTES_PER_TET_UPDATE = 92.0   # algorithmic bytes per local face update
 BYTES_PER_ADJ_NODE = 130.0    # algorithmic bytes per vertex of the adjoint
 
@@ -143,6 +147,8 @@ def main():
     ap.add_argument("--local", choices=["exact", "fista"], default="exact")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=BATCH,
+                    help="problems per step (multi-start: independent parameter sets in one pass)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 0)
 
@@ -180,10 +186,27 @@ def main():
     opts = gbp.make_opts(local_solver=gbp.LOCAL_FISTA if args.local == "fista" else gbp.LOCAL_EXACT, n_f=32)
     prec = gbp.PREC_BF16 if args.precision == "bf16" else gbp.PREC_FP32
     out = None
+    B = max(1, args.batch)
+    if B > 1:
+        # B starts of the same inverse problem: the prior-mean point with a
+        # global velocity scale exp(N(0, 0.1)) and onset times 10 ms + U(-2, 2)
+        # per start (start 0 is the prior-mean point itself)
+        r = np.random.default_rng(1234)
+        sc_f = np.concatenate([[1.0], np.exp(r.normal(0, 0.1, B - 1))]).astype(np.float32)
+        sc_t = np.concatenate([[1.0], np.exp(r.normal(0, 0.1, B - 1))]).astype(np.float32)
+        cfB_np = np.stack([cf_np * sc_f[b] for b in range(B)])
+        ctB_np = np.stack([ct_np * sc_t[b] for b in range(B)])
+        tB_np = np.stack([ons.t] + [(ons.t + r.uniform(-2, 2, ons.K)).astype(np.float32) for _ in range(B - 1)])
+        tgB_np = np.stack([target_np.astype(np.float32)] * B)
+        cfB, ctB = torch.from_numpy(cfB_np).to(dev), torch.from_numpy(ctB_np).to(dev)
+        tB, tgB = torch.from_numpy(tB_np).to(dev), torch.from_numpy(tgB_np).to(dev)
 
     def step():
         nonlocal out
-        out = ctx.forward_backward(cf, ct, target, p.tmpl, t=t_on, opts=opts, precision=prec, out=out)
+        if B == 1:
+            out = ctx.forward_backward(cf, ct, target, p.tmpl, t=t_on, opts=opts, precision=prec, out=out)
+        else:
+            out = ctx.forward_backward_batch(cfB, ctB, tgB, p.tmpl, t=tB, opts=opts, precision=prec, out=out)
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
     for _ in range(args.warmup):
@@ -219,6 +242,24 @@ def main():
     kt_ms, kt_n = ctx.kernel_times(6)
     ctx.enable_timing(False)
     st = ctx.stats()
+    single = None
+    if B > 1:
+        # one evaluation per step (gbp_forward_backward), same timing rules
+        s_out = None
+        for _ in range(max(3, args.warmup)):
+            s_out = ctx.forward_backward(cf, ct, target, p.tmpl, t=t_on, opts=opts, precision=prec, out=s_out)
+            flush.zero_()
+        s_ms = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s_out = ctx.forward_backward(cf, ct, target, p.tmpl, t=t_on, opts=opts, precision=prec, out=s_out)
+            e1.record(stream)
+            flush.zero_()
+            torch.cuda.synchronize()
+            s_ms.append(e0.elapsed_time(e1))
+        single = {"value": world * 1e3 * len(s_ms) / sum(s_ms), "unit": "evals/s",
+                  "ms_per_step": sum(s_ms) / len(s_ms), "batch": 1}
     total_s = sum(ms_steps) / 1e3
     if dist is not None:
         tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
@@ -228,7 +269,39 @@ def main():
 
     # e2e: the same evaluation from host buffers through gbp_forward_backward_host
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and B > 1:
+        # the batch through the same entry point, inputs copied from pinned
+        # host memory and outputs read back inside the timed region
+        hin = [torch.from_numpy(a).pin_memory() for a in (cfB_np, ctB_np, tB_np, tgB_np)]
+        din = [torch.empty_like(h, device=dev) for h in hin]
+        outs = ("loss", "d_cf", "d_ct", "d_t", "d_x")
+
+        def e2e_step():
+            nonlocal out
+            for h, d in zip(hin, din):
+                d.copy_(h, non_blocking=True)
+            out = ctx.forward_backward_batch(din[0], din[1], din[3], p.tmpl, t=din[2], opts=opts, precision=prec,
+                                             out=out)
+            res = [out[k].to("cpu", non_blocking=True) for k in outs]
+            torch.cuda.synchronize()
+            return res
+
+        for _ in range(2):
+            e2e_step()
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * B * args.steps / e2e_s, "unit": "evals/s",
+               "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hin)),
+               "d2h_bytes_per_step": int(sum(out[k].numel() * 4 for k in outs))}
+    if not args.no_e2e and B == 1:
         h_out = None
         for _ in range(2):
             h_out = ctx.forward_backward_host(cf_np, ct_np, target_np, p.tmpl, t=ons.t, opts=opts,
@@ -260,9 +333,9 @@ def main():
     adj_ms = kt_ms[4] / max(kt_n[4], 1)
     face_updates = st["face_updates"]
     achieved = face_updates * BYTES_PER_TET_UPDATE / (fim_ms / 1e3) / 1e9
-    adj_achieved = p.mesh.n_v * BYTES_PER_ADJ_NODE / (adj_ms / 1e3) / 1e9
+    adj_achieved = B * p.mesh.n_v * BYTES_PER_ADJ_NODE / (adj_ms / 1e3) / 1e9
     ms_per_step = 1e3 * total_s / steps
-    value = world * steps / total_s
+    value = world * B * steps / total_s
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         from oracle import oracle as O
@@ -270,14 +343,14 @@ def main():
         cpu = {"value": 1.0 / t_cpu, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
                "sample": "one full evaluation of the same workload (FP64 oracle: worklist Gauss-Seidel "
                          "eikonal single-threaded, ECG / misfit OpenMP, SCC adjoint serial)",
-               "seconds": t_cpu, "loss_gpu": float(out["loss"].item()), "loss_oracle": r["loss"]}
+               "seconds": t_cpu, "loss_gpu": float(out["loss"].reshape(-1)[0].item()), "loss_oracle": r["loss"]}
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "fim_traffic.json")
+    prof = os.path.join(ROOT, "profiles", "fim_traffic_c3_batch8.txt")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
                 tj = json.load(f)
-            if tj.get("kernel_hash") == kernel_hash():
+            if tj.get("kernel_hash") == kernel_hash() and tj.get("batch") == B and tj.get("n") == args.n:
                 traffic = tj.get("bytes_per_launch")
         except Exception:
             traffic = None
@@ -296,7 +369,7 @@ def main():
         "data": "synthetic",
         "config": dict(workload_config(args.n), n_v=p.mesh.n_v, n_t=p.mesh.n_t, leads=int(p.L.shape[0]),
                        T=p.tmpl.T, onsets=p.onsets.K, local_solver=args.local, precision=args.precision,
-                       l2="flushed between steps (256 MB write)", parallelism="replicas"),
+                       batch=B, l2="flushed between steps (256 MB write)", parallelism="replicas"),
         "tet_updates_per_s": world * face_updates * steps / total_s,
         "fim": {"iterations": st["iterations"], "face_updates": face_updates, "candidates": st["candidates"],
                 "fp64_fallbacks": st["fp64_fallbacks"], "ms": fim_ms},
@@ -312,6 +385,7 @@ def main():
                      "peak_source": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "single": single,
         "clocks": clocks,
         "gpu_launches": int(launches),
         "wall_s": wall,

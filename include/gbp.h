@@ -217,6 +217,28 @@ gbp_status gbp_forward_backward_host(gbp_ctx *ctx, const gbp_solve_opts *opts,
                                      const float *target, float *loss, float *d_cf,
                                      float *d_ct, float *d_t, float *d_x);
 
+/* B independent evaluations on the same mesh, fibres, lead field and onset
+ * sites in one pass (multi-start: the paper suggests several starts against
+ * local minima of the inverse problem, Sec. IV).  Each problem b has its own
+ * velocities, onset times and target; the FIM, the parent pass and the
+ * adjoint run all B problems in the same launches, so their per-iteration
+ * latency is shared.  cf, ct device float32 [B][n_t]; t device float32
+ * [B][K] (NULL: every problem uses the times of gbp_set_onsets); target
+ * device float32 [B][N][T]; outputs device: loss [B], ecg [B][N][T] (may be
+ * NULL), d_cf, d_ct [B][n_t], d_t [B][K], d_x [B][K][3] (any may be NULL).
+ * Requires B * n_v < 2^31 / 3 and N * T <= 51200.  Grows the context's
+ * per-problem arrays to B problems on first use (allocation, synchronises
+ * once).  Afterwards the single-problem state is reset: the next
+ * single-problem solve needs gbp_set_velocities first.  Statistics
+ * (gbp_get_solve_stats) add up over the B problems.  Errors:
+ * GBP_ERR_INVALID_ARG, GBP_ERR_STATE, GBP_ERR_CUDA and the device errors of
+ * gbp_eikonal_solve / gbp_geodesic_backward. */
+gbp_status gbp_forward_backward_batch(gbp_ctx *ctx, int32_t B, const gbp_solve_opts *opts,
+                                      const gbp_template *tmpl, int32_t precision, const float *cf,
+                                      const float *ct, const float *t, const float *target,
+                                      float *loss, float *ecg, float *d_cf, float *d_ct, float *d_t,
+                                      float *d_x);
+
 /* ------------------------------------------------------------------ */
 /* learned initialiser: network training and inference kernels          */
 /* ------------------------------------------------------------------ */

@@ -34,8 +34,13 @@
 
 namespace gbp {
 
+// Batched: vertex entries g = b * n_v + i and tet entries b * n_t + j of
+// problem b; the mesh and the onset sites are shared.
 struct AdjArgs {
-    int64_t n_v;
+    int64_t n_v;    // vertices per problem
+    int64_t n_t;    // tets per problem
+    int64_t n_tot;  // n_v x problems
+    int K;
     const float4 *xyz;
     const int4 *tets;
     const float4 *tm;
@@ -55,7 +60,7 @@ struct AdjArgs {
 };
 
 __device__ __forceinline__ void velocity_terms(float3 w, float4 m, float cfj, float ctj, float mu, float *d_cf,
-                                               float *d_ct, int j)
+                                               float *d_ct, int64_t j)
 {
     float fw = m.x * w.x + m.y * w.y + m.z * w.z;
     float3 wp = make_float3(w.x - fw * m.x, w.y - fw * m.y, w.z - fw * m.z);
@@ -68,10 +73,12 @@ __device__ __forceinline__ void velocity_terms(float3 w, float4 m, float cfj, fl
     if (d_ct) atomicAdd(&d_ct[j], -mu * wp2 * ict * ict * ict * ig);
 }
 
-// gradient contributions of vertex i's own parent (no pushes)
-__device__ __forceinline__ void local_terms(const AdjArgs &a, int64_t i, int4 r, float m)
+// gradient contributions of vertex i (of problem b) through its own parent
+// (no pushes)
+__device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, int4 r, float m)
 {
     const int code = r.x;
+    const int64_t toff = (int64_t)b * a.n_t;
     if (code >= 0) {
         const int j = code >> 2, s = code & 3;
         const int4 tv = __ldg(&a.tets[j]);
@@ -90,10 +97,12 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int64_t i, int4 r,
             w.z = fmaf(-al[q3], xq.z - xi.z, w.z);
             ++q3;
         }
-        velocity_terms(w, __ldg(&a.tm[j]), __ldg(&a.cf[j]), __ldg(&a.ct[j]), m, a.d_cf, a.d_ct, j);
+        velocity_terms(w, __ldg(&a.tm[toff + j]), __ldg(&a.cf[toff + j]), __ldg(&a.ct[toff + j]), m, a.d_cf, a.d_ct,
+                       toff + j);
     } else if (code != GBP_UNREACHED) {
         const int k = -1 - code;
-        if (a.d_t) atomicAdd(&a.d_t[k], m);
+        const int bk = b * a.K + k;
+        if (a.d_t) atomicAdd(&a.d_t[bk], m);
         if (a.onset_kind == GBP_ONSET_ELEMENT) {
             const int E = __ldg(&a.on_idx[k]);
             const int4 tv = __ldg(&a.tets[E]);
@@ -109,8 +118,8 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int64_t i, int4 r,
                 w.y = fmaf(b, xi.y - xq.y, w.y);
                 w.z = fmaf(b, xi.z - xq.z, w.z);
             }
-            const float4 mm = __ldg(&a.tm[E]);
-            const float cfe = __ldg(&a.cf[E]), cte = __ldg(&a.ct[E]);
+            const float4 mm = __ldg(&a.tm[toff + E]);
+            const float cfe = __ldg(&a.cf[toff + E]), cte = __ldg(&a.ct[toff + E]);
             float fw = mm.x * w.x + mm.y * w.y + mm.z * w.z;
             float3 wp = make_float3(w.x - fw * mm.x, w.y - fw * mm.y, w.z - fw * mm.z);
             float icf = 1.f / cfe, ict = 1.f / cte;
@@ -120,11 +129,11 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int64_t i, int4 r,
                 float ig = 1.f / g;
                 if (a.d_x) {
                     float c1 = ict * ict, c2 = fw * icf * icf;
-                    atomicAdd(&a.d_x[3 * k + 0], -m * (wp.x * c1 + c2 * mm.x) * ig);
-                    atomicAdd(&a.d_x[3 * k + 1], -m * (wp.y * c1 + c2 * mm.y) * ig);
-                    atomicAdd(&a.d_x[3 * k + 2], -m * (wp.z * c1 + c2 * mm.z) * ig);
+                    atomicAdd(&a.d_x[3 * bk + 0], -m * (wp.x * c1 + c2 * mm.x) * ig);
+                    atomicAdd(&a.d_x[3 * bk + 1], -m * (wp.y * c1 + c2 * mm.y) * ig);
+                    atomicAdd(&a.d_x[3 * bk + 2], -m * (wp.z * c1 + c2 * mm.z) * ig);
                 }
-                velocity_terms(w, mm, cfe, cte, m, a.d_cf, a.d_ct, E);
+                velocity_terms(w, mm, cfe, cte, m, a.d_cf, a.d_ct, toff + E);
             }
         }
     }
@@ -170,16 +179,17 @@ __global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const floa
     }
 }
 
-__global__ void k_adj_count(int64_t n_v, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
+__global__ void k_adj_count(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
                             unsigned long long *w)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_v) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_tot) return;
     int4 r = rec[i];
     if (r.x < 0) return;
+    const int boff = (i / n_v) * n_v;
     int j = r.x >> 2, s = r.x & 3;
     int4 tv = tets[j];
-    int ids[4] = {tv.x, tv.y, tv.z, tv.w};
+    int ids[4] = {boff + tv.x, boff + tv.y, boff + tv.z, boff + tv.w};
     int al[3] = {r.y, r.z, r.w};
     int q3 = 0;
 #pragma unroll
@@ -236,11 +246,15 @@ __device__ __forceinline__ void st_release_i32(int *p, int v)
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+#ifndef GBP_ADJ_REFILL
+#define GBP_ADJ_REFILL 8  // idle lanes that make a warp take new items while others are busy
+#endif
+
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
 {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-    const int64_t n_v = a.n_v;
+    const int64_t n_v = a.n_v, n_tot = a.n_tot;
     unsigned int nbar = 0;
     __shared__ int s_proc;
     if (threadIdx.x == 0) s_proc = 0;
@@ -250,7 +264,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     if (tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[0]));
     // ---- dataflow phase (no grid barrier per level) ----
     // The vertices readied so far sit in a work queue of (vertex, mu) items
-    // (lists[0..2 n_v) as n_v 64-bit slots, empty = all ones); q_res counts
+    // (lists[0..2 n_tot) as n_tot 64-bit slots, empty = all ones); q_res counts
     // the slots produced, q_head the slots handed out, and q_active the
     // queued items plus chains in progress (it reaches zero only when no
     // more work can appear).  Each warp runs up to 32 chains in lockstep:
@@ -271,7 +285,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     for (;;) {
         // hand available slots to the idle lanes
         const unsigned int idle = __ballot_sync(0xffffffffu, v < 0 && pending < 0);
-        if (idle) {
+        // a refill costs the busy lanes a round trip: batch it
+        if (idle && (__popc(idle) >= GBP_ADJ_REFILL || idle == 0xffffffffu ||
+                     !__ballot_sync(0xffffffffu, v >= 0))) {
             int base = 0, got = 0;
             if (lane == 0) {
                 const int avail = ld_relaxed_i32(&a.ctl->q_res) - ld_relaxed_i32(&a.ctl->q_head);
@@ -286,18 +302,20 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         // a slot handed out may still be empty if other warps took the items
         // counted as available; it fills once its producer stores it
         if (pending >= 0) {
-            const unsigned long long item = pending < n_v ? ld_relaxed_u64(&queue[pending]) : 0ull;
-            if (pending >= n_v) {
-                pending = -1;  // cannot happen: at most n_v items are ever queued
+            const unsigned long long item = pending < n_tot ? ld_relaxed_u64(&queue[pending]) : 0ull;
+            if (pending >= n_tot) {
+                pending = -1;  // cannot happen: at most n_tot items are ever queued
             } else if (item != ~0ull) {
                 v = (int)(unsigned int)(item & 0xffffffffu);
                 m = __uint_as_float((unsigned int)(item >> 32));
                 pending = -1;
             }
         }
-        // one vertex per busy lane
+        // one vertex per busy lane (entry v = b * n_v + vertex)
         int ended = 0;
         if (v >= 0) {
+            const int b = v / (int)n_v;
+            const int boff = b * (int)n_v;
             const int4 r = __ldg(&a.rec[v]);
             a.mu[v] = m;
             a.proc[v] = 1;
@@ -308,8 +326,12 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                 const int j = r.x >> 2, s = r.x & 3;
                 const int4 tv = __ldg(&a.tets[j]);
                 const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-                const int f[3] = {s == 0 ? tv.y : tv.x, s <= 1 ? tv.z : tv.y, s <= 2 ? tv.w : tv.z};
+                const int f[3] = {boff + (s == 0 ? tv.y : tv.x), boff + (s <= 1 ? tv.z : tv.y),
+                                  boff + (s <= 2 ? tv.w : tv.z)};
                 unsigned long long nw[3] = {0ull, 0ull, 0ull};
+                float lp[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) lp[q] = al[q] != 0.f ? __ldg(&a.lam[f[q]]) : 0.f;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     if (al[q] == 0.f) continue;
@@ -317,12 +339,12 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                     const unsigned long long d = (unsigned long long)c - ADJ_ONE;
                     nw[q] = atomicAdd(&a.w[f[q]], d) + d;
                 }
-                local_terms(a, v, r, m);
+                local_terms(a, b, v - boff, r, m);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     if (al[q] == 0.f || adj_count(nw[q]) != 0u) continue;
                     // this push completed f[q]: its mu is lambda plus the whole sum
-                    const float mp = __ldg(&a.lam[f[q]]) + (float)((double)adj_sum(nw[q]) * iscale);
+                    const float mp = lp[q] + (float)((double)adj_sum(nw[q]) * iscale);
                     if (next < 0) {
                         next = f[q];
                         mnext = mp;
@@ -333,7 +355,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                     }
                 }
             } else {
-                local_terms(a, v, r, m);
+                local_terms(a, b, v - boff, r, m);
             }
             v = next;
             m = mnext;
@@ -397,10 +419,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     // ---- vertices blocked by cycles: fixed-point iteration ----
     // collect the unprocessed reached vertices R (closed under parents); the
     // barrier above ordered every write of the dataflow phase before this
-    int *R = a.lists + 2 * n_v;
-    for (int64_t base = 0; base < n_v; base += nth) {
+    int *R = a.lists + 2 * n_tot;
+    for (int64_t base = 0; base < n_tot; base += nth) {
         const int64_t i = base + tid;
-        bool app = i < n_v && __ldcg(&a.proc[i]) == 0;
+        bool app = i < n_tot && __ldcg(&a.proc[i]) == 0;
         if (app) {
             // base value: lambda plus the pushes of the processed children
             const float b0 = __ldg(&a.lam[i]) + (float)((double)adj_sum(__ldcg(&a.w[i])) * iscale);
@@ -424,12 +446,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     auto push = [&](int i, float x, float *dst) {
         const int4 r = __ldg(&a.rec[i]);
         if (r.x < 0) return;
+        const int boff = (i / (int)n_v) * (int)n_v;
         const int j = r.x >> 2, s = r.x & 3;
         const int4 tv = __ldg(&a.tets[j]);
         const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-        const int f0 = s == 0 ? tv.y : tv.x;
-        const int f1 = s <= 1 ? tv.z : tv.y;
-        const int f2 = s <= 2 ? tv.w : tv.z;
+        const int f0 = boff + (s == 0 ? tv.y : tv.x);
+        const int f1 = boff + (s <= 1 ? tv.z : tv.y);
+        const int f2 = boff + (s <= 2 ? tv.w : tv.z);
         if (al[0] != 0.f) atomicAdd(&dst[f0], al[0] * x);
         if (al[1] != 0.f) atomicAdd(&dst[f1], al[1] * x);
         if (al[2] != 0.f) atomicAdd(&dst[f2], al[2] * x);
@@ -490,7 +513,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         const float x = ld_cg_f(&a.xj[i]);
         a.mu[i] = x;
         a.proc[i] = 1;
-        local_terms(a, i, __ldg(&a.rec[i]), x);
+        const int b = i / (int)n_v;
+        local_terms(a, b, i - b * (int)n_v, __ldg(&a.rec[i]), x);
     }
 }
 
@@ -511,30 +535,34 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->q_active, 0, sizeof(int), c->stream);
     if (err) return err;
-    err = cudaMemsetAsync(c->lists, 0xff, sizeof(unsigned long long) * n_v, c->stream);  // empty queue slots
+    const int64_t n_tot = n_v * c->nb;
+    err = cudaMemsetAsync(c->lists, 0xff, sizeof(unsigned long long) * n_tot, c->stream);  // empty queue slots
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->adj_levels, 0, offsetof(Control, adj_ts) - offsetof(Control, adj_levels),
                           c->stream);
     if (err) return err;
-    if (d_cf) cudaMemsetAsync(d_cf, 0, sizeof(float) * c->n_t, c->stream);
-    if (d_ct) cudaMemsetAsync(d_ct, 0, sizeof(float) * c->n_t, c->stream);
-    if (d_t) cudaMemsetAsync(d_t, 0, sizeof(float) * c->K, c->stream);
-    if (d_x) cudaMemsetAsync(d_x, 0, sizeof(float) * 3 * c->K, c->stream);
+    if (d_cf) cudaMemsetAsync(d_cf, 0, sizeof(float) * c->n_t * c->nb, c->stream);
+    if (d_ct) cudaMemsetAsync(d_ct, 0, sizeof(float) * c->n_t * c->nb, c->stream);
+    if (d_t) cudaMemsetAsync(d_t, 0, sizeof(float) * c->K * c->nb, c->stream);
+    if (d_x) cudaMemsetAsync(d_x, 0, sizeof(float) * 3 * c->K * c->nb, c->stream);
     int th = 256;
-    unsigned bl = (unsigned)((n_v + th - 1) / th);
+    unsigned bl = (unsigned)((n_tot + th - 1) / th);
     time_begin(c, 4);
-    k_adj_init<<<bl, th, 0, c->stream>>>(n_v, c->rec, dphi, c->adj_w, c->proc, c->ctl);
-    k_adj_count<<<bl, th, 0, c->stream>>>(n_v, c->rec, c->tets, c->adj_w);
+    k_adj_init<<<bl, th, 0, c->stream>>>(n_tot, c->rec, dphi, c->adj_w, c->proc, c->ctl);
+    k_adj_count<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_w);
     if (c->max_nbr > ADJ_MAX_CHILDREN) {
-        k_adj_check<<<bl, th, 0, c->stream>>>(n_v, c->adj_w, c->ctl);
+        k_adj_check<<<bl, th, 0, c->stream>>>(n_tot, c->adj_w, c->ctl);
         c->launches++;
     }
-    k_adj_seed<<<bl, th, 0, c->stream>>>(n_v, c->adj_w, c->proc, dphi,
+    k_adj_seed<<<bl, th, 0, c->stream>>>(n_tot, c->adj_w, c->proc, dphi,
                                          reinterpret_cast<unsigned long long *>(c->lists), c->ctl);
     c->launches += 3;
     if ((err = cudaGetLastError())) return err;
     AdjArgs a;
     a.n_v = n_v;
+    a.n_t = c->n_t;
+    a.n_tot = n_tot;
+    a.K = c->K;
     a.xyz = c->xyz;
     a.tets = c->tets;
     a.tm = c->tm;

@@ -349,6 +349,8 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
         c->n_v = c->n_t = 0;
         return from_cuda(err);
     }
+    c->nb = 1;
+    c->nb_cap = 1;
     c->param_gen++;
     return GBP_OK;
 }
@@ -372,6 +374,7 @@ gbp_status gbp_set_velocities(gbp_ctx *c, const float *cf, const float *ct)
     if (!c || !cf || !ct) return GBP_ERR_INVALID_ARG;
     if (!c->n_t || !c->has_fib) return GBP_ERR_STATE;
     DeviceGuard g(c->device);
+    c->nb = 1;  // one problem from here on
     cudaError_t e = cudaSuccess;
     if (cf != c->cf) e = cudaMemcpyAsync(c->cf, cf, sizeof(float) * c->n_t, cudaMemcpyDeviceToDevice, c->stream);
     if (!e && ct != c->ct)
@@ -420,7 +423,7 @@ gbp_status gbp_set_onsets(gbp_ctx *c, int32_t kind, int32_t K, const int32_t *id
     if (K != c->K) {
         e = dalloc(&c->on_idx, K);
         if (!e) e = dalloc(&c->on_bary, 4 * K);
-        if (!e) e = dalloc(&c->on_t, K);
+        if (!e) e = dalloc(&c->on_t, (int64_t)K * c->nb_cap);
     }
     if (!e) e = cudaMemcpyAsync(c->on_idx, idx, sizeof(int) * K, cudaMemcpyDeviceToDevice, c->stream);
     if (!e && kind == GBP_ONSET_ELEMENT)
@@ -607,6 +610,115 @@ gbp_status gbp_forward_backward_host(gbp_ctx *c, const gbp_solve_opts *opts, con
     if (d_t) std::memcpy(d_t, po + 1 + 2 * n_t, sizeof(float) * K);
     if (d_x) std::memcpy(d_x, po + 1 + 2 * n_t + K, sizeof(float) * 3 * K);
     return GBP_OK;
+}
+
+// Grow the per-problem arrays to hold B problems (contents are not kept).
+static cudaError_t ensure_batch(gbp_ctx *c, int B)
+{
+    if (B <= c->nb_cap) return cudaSuccess;
+    const int64_t nv = c->n_v * B, nt = c->n_t * B;
+    cudaError_t err = cudaSuccess;
+#define CK(x)                                \
+    do {                                     \
+        if (!err) err = (x);                 \
+    } while (0)
+    CK(cudaStreamSynchronize(c->stream));
+    CK(dalloc(&c->cf, nt));
+    CK(dalloc(&c->ct, nt));
+    CK(dalloc(&c->tm, nt));
+    CK(dalloc(&c->tsd, nt));
+    CK(dalloc(&c->tlip, nt));
+    CK(dalloc(&c->phi, nv));
+    CK(dalloc(&c->rec, nv));
+    CK(dalloc(&c->chg, nv));
+    CK(dalloc(&c->stamp, nv));
+    CK(dalloc(&c->lists, 3 * nv + 32));
+    CK(dalloc(&c->keys, nv));
+    CK(dalloc(&c->mu, nv));
+    CK(dalloc(&c->jac_x, nv));
+    CK(dalloc(&c->jac_acc, nv));
+    CK(dalloc(&c->jac_acc2, nv));
+    CK(dalloc(&c->adj_w, nv));
+    CK(dalloc(&c->proc, nv));
+    CK(dalloc(&c->dphi, nv));
+    if (c->K) CK(dalloc(&c->on_t, (int64_t)c->K * B));
+#undef CK
+    c->has_vel = false;
+    c->lip_valid = false;
+    c->solve_gen = -1;
+    c->param_gen++;
+    if (err) {
+        c->nb_cap = 0;  // every per-problem array must be rebuilt by a new mesh upload
+        return err;
+    }
+    c->nb_cap = B;
+    return cudaSuccess;
+}
+
+gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opts *opts, const gbp_template *tmpl,
+                                      int32_t precision, const float *cf, const float *ct, const float *t,
+                                      const float *target, float *loss, float *ecg, float *d_cf, float *d_ct,
+                                      float *d_t, float *d_x)
+{
+    if (!c || B < 1 || !cf || !ct || !target || !loss || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
+    if (precision != GBP_PREC_FP32 && precision != GBP_PREC_BF16) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v || !c->has_fib || !c->K || !c->N || c->nb_cap < 1) return GBP_ERR_STATE;
+    if ((int64_t)B * c->n_v >= (1ll << 31) / 3 || (int64_t)B * c->n_t >= (1ll << 31)) return GBP_ERR_INVALID_ARG;
+    if ((int64_t)c->N * tmpl->T > 51200) return GBP_ERR_INVALID_ARG;
+    gbp_solve_opts o = normalized_opts(c, opts);
+    if (o.local_solver != GBP_LOCAL_EXACT && o.local_solver != GBP_LOCAL_FISTA) return GBP_ERR_INVALID_ARG;
+    if (o.local_solver == GBP_LOCAL_FISTA && (o.n_f < 1 || o.n_f > 256)) return GBP_ERR_INVALID_ARG;
+    if (!(o.eps >= 0.f) || !std::isfinite(o.eps)) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaError_t e = ensure_batch(c, B);
+    if (e) return from_cuda(e);
+    const int64_t n_v = c->n_v, n_t = c->n_t, K = c->K, NT = (int64_t)c->N * tmpl->T;
+    float *V = ecg;
+    if (!V) {
+        if (NT * B > c->ecg_tmp_cap) {
+            e = dalloc(&c->ecg_tmp, NT * B);
+            if (e) return from_cuda(e);
+            c->ecg_tmp_cap = NT * B;
+        }
+        V = c->ecg_tmp;
+    }
+    c->nb = B;
+    e = cudaMemcpyAsync(c->cf, cf, sizeof(float) * n_t * B, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->ct, ct, sizeof(float) * n_t * B, cudaMemcpyDeviceToDevice, c->stream);
+    if (t) {
+        if (!e) e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * K * B, cudaMemcpyDeviceToDevice, c->stream);
+    } else {
+        for (int b = 1; b < B && !e; ++b)
+            e = cudaMemcpyAsync(c->on_t + b * K, c->on_t, sizeof(float) * K, cudaMemcpyDeviceToDevice, c->stream);
+    }
+    if (!e) e = cudaMemsetAsync(&c->ctl->param_status, 0, sizeof(int), c->stream);
+    if (!e) {
+        gbp::time_begin(c, 5);
+        e = gbp::launch_precompute(c);
+        gbp::time_end(c, 5);
+    }
+    if (!e && o.local_solver == GBP_LOCAL_FISTA) {
+        gbp::time_begin(c, 5);
+        e = gbp::launch_lipschitz(c);
+        gbp::time_end(c, 5);
+    }
+    if (!e) e = gbp::launch_fim(c, &o);
+    if (!e) e = gbp::launch_parent_pass(c, o.local_solver, o.n_f, nullptr, nullptr, nullptr);
+    for (int b = 0; b < B && !e; ++b) {
+        e = gbp::launch_ecg_forward(c, c->phi + b * n_v, tmpl, precision, V + b * NT);
+        if (!e)
+            e = gbp::launch_ecg_backward(c, c->phi + b * n_v, V + b * NT, target + b * NT, tmpl, loss + b,
+                                         c->dphi + b * n_v);
+    }
+    if (!e) e = gbp::launch_adjoint(c, c->dphi, d_cf, d_ct, d_t, d_x);
+    // the context's single-problem state is gone: the next single-problem
+    // evaluation starts from gbp_set_velocities
+    c->nb = 1;
+    c->has_vel = false;
+    c->lip_valid = false;
+    c->solve_gen = -1;
+    c->param_gen++;
+    return from_cuda(e);
 }
 
 gbp_status gbp_local_solve_batch(gbp_ctx *c, int64_t n, const float *e, const float *fib, const float *cf,

@@ -8,15 +8,17 @@ namespace gbp {
 // ---------------------------------------------------------------------------
 // per-tet metric (Sec. II-A): R = D^{1/2} in factored form
 // ---------------------------------------------------------------------------
-__global__ void k_precompute(int64_t n_t, const float *__restrict__ fib, const float *__restrict__ cf,
+// Batched: entry g = b * n_t + j of the per-problem arrays (cf, ct, tm, tsd).
+__global__ void k_precompute(int64_t n_t, int64_t n_tot, const float *__restrict__ fib, const float *__restrict__ cf,
                              const float *__restrict__ ct, float4 *__restrict__ tm, float *__restrict__ tsd,
                              Control *ctl)
 {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n_t) return;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_tot) return;
+    const int64_t j = g % n_t;
     float fx = fib[3 * j], fy = fib[3 * j + 1], fz = fib[3 * j + 2];
     float nn = sqrtf(fx * fx + fy * fy + fz * fz);
-    float vf = cf[j], vt = ct[j];
+    float vf = cf[g], vt = ct[g];
     bool bad = !(nn > 0.f) || !(vf > 0.f) || !(vt > 0.f) || !isfinite(vf) || !isfinite(vt) || !isfinite(nn);
     if (bad) {
         atomicCAS(&ctl->param_status, 0, (int)GBP_ERR_NOT_SPD);
@@ -25,15 +27,16 @@ __global__ void k_precompute(int64_t n_t, const float *__restrict__ fib, const f
     }
     float in = 1.f / nn;
     float sa = 1.f / vt;
-    tm[j] = make_float4(fx * in, fy * in, fz * in, sa);
-    tsd[j] = 1.f / vf - sa;
+    tm[g] = make_float4(fx * in, fy * in, fz * in, sa);
+    tsd[g] = 1.f / vf - sa;
 }
 
 cudaError_t launch_precompute(gbp_ctx *c)
 {
     int th = 256;
-    int64_t bl = (c->n_t + th - 1) / th;
-    k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, c->fib, c->cf, c->ct, c->tm, c->tsd, c->ctl);
+    const int64_t n_tot = c->n_t * c->nb;
+    int64_t bl = (n_tot + th - 1) / th;
+    k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->fib, c->cf, c->ct, c->tm, c->tsd, c->ctl);
     c->launches++;
     return cudaGetLastError();
 }
@@ -63,14 +66,14 @@ __device__ __forceinline__ void face_vectors(const float4 *__restrict__ xyz, int
     p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
 }
 
-__global__ void k_lipschitz(int64_t n_t, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
+__global__ void k_lipschitz(int64_t n_t, int64_t n_tot, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
                             const float4 *__restrict__ tm, const float *__restrict__ tsd, float4 *__restrict__ tlip)
 {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n_t) return;
-    int4 tv = tets[j];
-    float4 m = tm[j];
-    float sd = tsd[j];
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_tot) return;
+    int4 tv = tets[g % n_t];
+    float4 m = tm[g];
+    float sd = tsd[g];
     float L[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -79,14 +82,15 @@ __global__ void k_lipschitz(int64_t n_t, const float4 *__restrict__ xyz, const i
         face_vectors(xyz, tv, s, m, sd, p, fv);
         L[s] = face_lipschitz(p);
     }
-    tlip[j] = make_float4(L[0], L[1], L[2], L[3]);
+    tlip[g] = make_float4(L[0], L[1], L[2], L[3]);
 }
 
 cudaError_t launch_lipschitz(gbp_ctx *c)
 {
     int th = 256;
-    int64_t bl = (c->n_t + th - 1) / th;
-    k_lipschitz<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, c->xyz, c->tets, c->tm, c->tsd, c->tlip);
+    const int64_t n_tot = c->n_t * c->nb;
+    int64_t bl = (n_tot + th - 1) / th;
+    k_lipschitz<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->xyz, c->tets, c->tm, c->tsd, c->tlip);
     c->launches++;
     return cudaGetLastError();
 }
@@ -95,20 +99,24 @@ cudaError_t launch_lipschitz(gbp_ctx *c)
 // onset seeding (Algorithm 2 initialisation, Eq. upwind_xi)
 // ---------------------------------------------------------------------------
 
-__global__ void k_onset_keys(int K, int kind, const int *__restrict__ idx, const float *__restrict__ bary,
+// Batched: thread g = b * K + k (onset times t [nb][K]; sites shared).
+__global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ idx, const float *__restrict__ bary,
                              const float *__restrict__ t, int64_t n_v, int64_t n_t, const float4 *__restrict__ xyz,
                              const int4 *__restrict__ tets, const float4 *__restrict__ tm,
-                             const float *__restrict__ tsd, unsigned long long *keys, Control *ctl)
+                             const float *__restrict__ tsd, unsigned long long *keys_all, Control *ctl)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= K * nb) return;
+    const int b = g / K, k = g - b * K;
+    unsigned long long *keys = keys_all + (int64_t)b * n_v;
+    const float tk = t[g];
     int id = idx[k];
     if (kind == GBP_ONSET_NODAL) {
         if (id < 0 || id >= n_v) {
             atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
             return;
         }
-        unsigned long long key = ((unsigned long long)float_key(t[k]) << 32) | (unsigned)k;
+        unsigned long long key = ((unsigned long long)float_key(tk) << 32) | (unsigned)k;
         atomicMin(&keys[id], key);
     } else {
         if (id < 0 || id >= n_t) {
@@ -127,12 +135,12 @@ __global__ void k_onset_keys(int K, int kind, const int *__restrict__ idx, const
             xo.y = fmaf(b, x[q].y, xo.y);
             xo.z = fmaf(b, x[q].z, xo.z);
         }
-        float4 m = tm[id];
-        float sd = tsd[id];
+        float4 m = tm[(int64_t)b * n_t + id];
+        float sd = tsd[(int64_t)b * n_t + id];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float3 w = xform(make_float3(x[q].x - xo.x, x[q].y - xo.y, x[q].z - xo.z), m, sd);
-            float v = t[k] + sqrtf(f3dot(w, w));
+            float v = tk + sqrtf(f3dot(w, w));
             unsigned long long key = ((unsigned long long)float_key(v) << 32) | (unsigned)k;
             atomicMin(&keys[ids[q]], key);
         }
@@ -159,13 +167,16 @@ __global__ void k_init_nodes(int64_t n_v, const unsigned long long *__restrict__
 }
 
 // Seeded vertices put their neighbours on the first active list.
-__global__ void k_seed_lists(int64_t n_v, const unsigned long long *__restrict__ keys, const int *__restrict__ n2n_ptr,
-                             const int *__restrict__ n2n, int *stamp, int *list1, Control *ctl)
+// Batched: vertex entry g = b * n_v + i (lists hold such entries).
+__global__ void k_seed_lists(int n_v, int n_tot, const unsigned long long *__restrict__ keys,
+                             const int *__restrict__ n2n_ptr, const int *__restrict__ n2n, int *stamp, int *list1,
+                             Control *ctl)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_v || keys[i] == ~0ull) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tot || keys[g] == ~0ull) return;
+    const int b = g / n_v, i = g - b * n_v;
     for (int e = n2n_ptr[i]; e < n2n_ptr[i + 1]; ++e) {
-        int m = n2n[e];
+        const int m = b * n_v + n2n[e];
         if (atomicMax(&stamp[m], 1) < 1) {
             int pos = atomicAdd(&ctl->count[1], 1);
             list1[pos] = m;
@@ -177,7 +188,9 @@ __global__ void k_seed_lists(int64_t n_v, const unsigned long long *__restrict__
 // persistent FIM (Algorithm 2)
 // ---------------------------------------------------------------------------
 struct FimArgs {
-    int64_t n_v;
+    int64_t n_v;    // vertices per problem
+    int64_t n_t;    // tets per problem
+    int64_t n_tot;  // n_v x problems (entries of the active lists)
     const float4 *xyz;
     const int4 *tets;
     const float4 *tm;
@@ -208,6 +221,9 @@ struct FimArgs {
 #ifndef GBP_FIM_G
 #define GBP_FIM_G 8  // lanes per active vertex
 #endif
+#ifndef GBP_FIM_R
+#define GBP_FIM_R 2  // faces per lane fetched together
+#endif
 #ifndef GBP_FIM_DYN
 #define GBP_FIM_DYN 0  // warps fetch active vertices from a counter (else a fixed stride)
 #endif
@@ -215,8 +231,12 @@ struct FimArgs {
 #define GBP_FIM_BLOCK 256  // threads per CTA
 #endif
 constexpr int FIM_G = GBP_FIM_G;
+constexpr int FIM_R = GBP_FIM_R;
 constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
-constexpr int FIM_MINB = 1024 / GBP_FIM_BLOCK;  // CTAs per SM at 64 registers
+#ifndef GBP_FIM_MINB
+#define GBP_FIM_MINB 3  // CTAs per SM (80 registers at 256 threads)
+#endif
+constexpr int FIM_MINB = GBP_FIM_MINB;
 constexpr int FIM_CAP = 2048;  // per-CTA append buffer (overflow goes straight to global)
 
 template <int MODE>
@@ -259,8 +279,8 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             a.ctl->fim_fetch[nxt] = 0;  // last used at k-2, next used at k+1
             s_cand += (unsigned long long)n_cand;
         }
-        const int *list = a.lists + (int64_t)cur * n_v;
-        int *nlist = a.lists + (int64_t)nxt * n_v;
+        const int *list = a.lists + (int64_t)cur * a.n_tot;
+        int *nlist = a.lists + (int64_t)nxt * a.n_tot;
 #if GBP_FIM_DYN
         for (;;) {
             int wbase = 0;
@@ -274,46 +294,84 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             const bool act = g < n_cand;
             if (!__any_sync(0xffffffffu, act)) break;
 #endif
-            int i = 0, beg = 0, end = 0;
+            // entry gi = b * n_v + i: vertex i of problem b
+            int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0;
+            int64_t toff = 0;
             float phi_old = 0.f;
+            float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
             if (act) {
-                i = __ldcg(&list[g]);
-                phi_old = __ldcg(&a.phi[i]);
+                gi = __ldcg(&list[g]);
+                const int b = gi / (int)n_v;
+                boff = b * (int)n_v;
+                toff = (int64_t)b * a.n_t;
+                i = gi - boff;
+                phi_old = __ldcg(&a.phi[gi]);
                 beg = __ldg(&a.n2t_ptr[i]);
                 end = __ldg(&a.n2t_ptr[i + 1]);
+                nb = __ldg(&a.n2n_ptr[i]);
+                ne = __ldg(&a.n2n_ptr[i + 1]);
+                xi = __ldg(&a.xyz[i]);
             }
             const int maxdeg = __reduce_max_sync(0xffffffffu, end - beg);
             float best = GBP_INF;
             int best_code = 0x7fffffff;
-            for (int e0 = 0; e0 < maxdeg; e0 += FIM_G) {
-                const int e = beg + e0 + sub;
-                if (e < end) {
-                    const int code = __ldg(&a.n2t[e]);
-                    const int j = code >> 2, s = code & 3;
-                    const int4 tv = __ldg(&a.tets[j]);
+            // FIM_R faces per lane at a time: their adjacency, tets and face
+            // values are fetched together (three dependent loads for all of
+            // them), then the masked ones are solved
+            for (int e0 = 0; e0 < maxdeg; e0 += FIM_G * FIM_R) {
+                int code[FIM_R];
+#pragma unroll
+                for (int r = 0; r < FIM_R; ++r) {
+                    const int e = beg + e0 + r * FIM_G + sub;
+                    code[r] = e < end ? __ldg(&a.n2t[e]) : -1;
+                }
+                int4 tv[FIM_R];
+#pragma unroll
+                for (int r = 0; r < FIM_R; ++r)
+                    tv[r] = code[r] >= 0 ? __ldg(&a.tets[code[r] >> 2]) : make_int4(0, 0, 0, 0);
+                float ph[FIM_R][3];
+                bool mk[FIM_R];
+#pragma unroll
+                for (int r = 0; r < FIM_R; ++r) {
+                    mk[r] = false;
+                    ph[r][0] = ph[r][1] = ph[r][2] = GBP_INF;
+                    if (code[r] >= 0) {
+                        int vi, f0, f1, f2;
+                        face_ids(tv[r], code[r] & 3, vi, f0, f1, f2);
+                        const int c0 = __ldcg(&a.chg[boff + f0]), c1 = __ldcg(&a.chg[boff + f1]),
+                                  c2 = __ldcg(&a.chg[boff + f2]);
+                        ph[r][0] = __ldcg(&a.phi[boff + f0]);
+                        ph[r][1] = __ldcg(&a.phi[boff + f1]);
+                        ph[r][2] = __ldcg(&a.phi[boff + f2]);
+                        mk[r] = max(c0, max(c1, c2)) >= k - 1;
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < FIM_R; ++r) {
+                    if (!mk[r]) continue;
+                    ++my_faces;
+                    const int code_r = code[r];
+                    const int j = code_r >> 2, s = code_r & 3;
+                    const float4 m = __ldg(&a.tm[toff + j]);
+                    const float sd = __ldg(&a.tsd[toff + j]);
                     int vi, f0, f1, f2;
-                    face_ids(tv, s, vi, f0, f1, f2);
-                    const int c0 = __ldcg(&a.chg[f0]), c1 = __ldcg(&a.chg[f1]), c2 = __ldcg(&a.chg[f2]);
-                    const float ph[3] = {__ldcg(&a.phi[f0]), __ldcg(&a.phi[f1]), __ldcg(&a.phi[f2])};
-                    if (max(c0, max(c1, c2)) >= k - 1) {
-                        ++my_faces;
-                        float3 p[3];
-                        const float4 m = __ldg(&a.tm[j]);
-                        const float sd = __ldg(&a.tsd[j]);
-                        int fv[3];
-                        face_vectors(a.xyz, tv, s, m, sd, p, fv);
-                        LocalRes r;
-                        if (MODE == GBP_LOCAL_FISTA) {
-                            const float4 Lq = __ldg(&a.tlip[j]);
-                            const float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
-                            r = local_fista(p, ph, Lv, a.n_f);
-                        } else {
-                            r = local_exact(p, ph, &fb_local);
-                        }
-                        if (r.v < best || (r.v == best && code < best_code)) {
-                            best = r.v;
-                            best_code = code;
-                        }
+                    face_ids(tv[r], s, vi, f0, f1, f2);
+                    const float4 x0 = __ldg(&a.xyz[f0]), x1 = __ldg(&a.xyz[f1]), x2 = __ldg(&a.xyz[f2]);
+                    float3 p[3];
+                    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
+                    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
+                    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
+                    LocalRes res;
+                    if (MODE == GBP_LOCAL_FISTA) {
+                        const float4 Lq = __ldg(&a.tlip[toff + j]);
+                        const float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
+                        res = local_fista(p, ph[r], Lv, a.n_f);
+                    } else {
+                        res = local_exact(p, ph[r], &fb_local);
+                    }
+                    if (res.v < best || (res.v == best && code_r < best_code)) {
+                        best = res.v;
+                        best_code = code_r;
                     }
                 }
             }
@@ -331,22 +389,18 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             if (act && best < phi_old) {
                 changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
                 if (sub == 0) {
-                    a.phi[i] = best;
-                    a.rec[i].x = best_code;
-                    if (changed) a.chg[i] = k;
+                    a.phi[gi] = best;
+                    a.rec[gi].x = best_code;
+                    if (changed) a.chg[gi] = k;
                 }
             }
             // activate the neighbours of changed vertices for iteration k+1
-            int nb = 0, ne = 0;
-            if (changed) {
-                nb = __ldg(&a.n2n_ptr[i]);
-                ne = __ldg(&a.n2n_ptr[i + 1]);
-            }
+            if (!changed) nb = ne = 0;
             const int maxn = __reduce_max_sync(0xffffffffu, ne - nb);
             for (int e0 = 0; e0 < maxn; e0 += FIM_G) {
                 const int e = nb + e0 + sub;
                 if (e < ne) {
-                    const int m = __ldg(&a.n2n[e]);
+                    const int m = boff + __ldg(&a.n2n[e]);
                     if (atomicMax(&a.stamp[m], k + 1) < k + 1) {
                         const int pos = atomicAdd(&s_n, 1);
                         if (pos < FIM_CAP) {
@@ -408,18 +462,19 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
 {
     cudaError_t err;
     const int64_t n_v = c->n_v;
+    const int64_t n_tot = n_v * c->nb;  // all problems of the batch (< 2^31, checked at set-up)
     // reset the control block (counters, status) and the onset keys; the
     // precompute's status word (last field) is kept
     err = cudaMemsetAsync(c->ctl, 0, offsetof(Control, param_status), c->stream);
     if (err) return err;
-    err = cudaMemsetAsync(c->keys, 0xff, sizeof(unsigned long long) * n_v, c->stream);
+    err = cudaMemsetAsync(c->keys, 0xff, sizeof(unsigned long long) * n_tot, c->stream);
     if (err) return err;
     int th = 256;
-    k_onset_keys<<<(c->K + th - 1) / th, th, 0, c->stream>>>(c->K, c->onset_kind, c->on_idx, c->on_bary, c->on_t,
-                                                              n_v, c->n_t, c->xyz, c->tets, c->tm, c->tsd, c->keys,
-                                                              c->ctl);
-    unsigned bl = (unsigned)((n_v + th - 1) / th);
-    k_init_nodes<<<bl, th, 0, c->stream>>>(n_v, c->keys, c->phi, c->rec, c->chg, c->stamp);
+    k_onset_keys<<<(c->K * c->nb + th - 1) / th, th, 0, c->stream>>>(c->K, c->nb, c->onset_kind, c->on_idx,
+                                                                      c->on_bary, c->on_t, n_v, c->n_t, c->xyz,
+                                                                      c->tets, c->tm, c->tsd, c->keys, c->ctl);
+    unsigned bl = (unsigned)((n_tot + th - 1) / th);
+    k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp);
     c->launches += 2;
     if ((err = cudaGetLastError())) return err;
     long long *trace = nullptr;
@@ -436,12 +491,15 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
             trace = c->trace;
         }
     }
-    k_seed_lists<<<bl, th, 0, c->stream>>>(n_v, c->keys, c->n2n_ptr, c->n2n, c->stamp, c->lists + n_v, c->ctl);
+    k_seed_lists<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->keys, c->n2n_ptr, c->n2n, c->stamp,
+                                           c->lists + n_tot, c->ctl);
     c->launches++;
     if ((err = cudaGetLastError())) return err;
 
     FimArgs a;
     a.n_v = n_v;
+    a.n_t = c->n_t;
+    a.n_tot = n_tot;
     a.xyz = c->xyz;
     a.tets = c->tets;
     a.tm = c->tm;
@@ -475,18 +533,26 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
 // ---------------------------------------------------------------------------
 // parent pass: alpha of the final parent face with the final values
 // ---------------------------------------------------------------------------
+// Batched: entry g = b * n_v + i.
 template <int MODE>
-__global__ void k_parent_pass(int64_t n_v, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
-                              const float4 *__restrict__ tm, const float *__restrict__ tsd,
-                              const float4 *__restrict__ tlip, int n_f, const float *__restrict__ phi, int4 *rec,
-                              float *out_phi, int32_t *out_parent, float *out_alpha, Control *ctl)
+__global__ void k_parent_pass(int n_v, int n_tot, int64_t n_t, const float4 *__restrict__ xyz,
+                              const int4 *__restrict__ tets, const float4 *__restrict__ tm_all,
+                              const float *__restrict__ tsd_all, const float4 *__restrict__ tlip_all, int n_f,
+                              const float *__restrict__ phi_all, int4 *rec, float *out_phi, int32_t *out_parent,
+                              float *out_alpha, Control *ctl)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_v) return;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tot) return;
+    const int b = g / n_v;
+    const float *phi = phi_all + (int64_t)b * n_v;
+    const float4 *tm = tm_all + (int64_t)b * n_t;
+    const float *tsd = tsd_all + (int64_t)b * n_t;
+    const float4 *tlip = tlip_all + (int64_t)b * n_t;
+    const int i = g;
     int4 r = rec[i];
     int code = r.x;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    float pv = phi[i];
+    float pv = phi_all[i];
     if (code >= 0) {
         int j = code >> 2, s = code & 3;
         int4 tv = tets[j];
@@ -522,14 +588,17 @@ __global__ void k_parent_pass(int64_t n_v, const float4 *__restrict__ xyz, const
 cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_t *parent, float *alpha)
 {
     int th = 256;
-    unsigned bl = (unsigned)((c->n_v + th - 1) / th);
+    const int n_tot = (int)(c->n_v * c->nb);
+    unsigned bl = (unsigned)((n_tot + th - 1) / th);
     time_begin(c, 1);
     if (mode == GBP_LOCAL_FISTA)
-        k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>(c->n_v, c->xyz, c->tets, c->tm, c->tsd, c->tlip,
-                                                                 n_f, c->phi, c->rec, phi, parent, alpha, c->ctl);
+        k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>((int)c->n_v, n_tot, c->n_t, c->xyz, c->tets, c->tm,
+                                                                 c->tsd, c->tlip, n_f, c->phi, c->rec, phi, parent,
+                                                                 alpha, c->ctl);
     else
-        k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>(c->n_v, c->xyz, c->tets, c->tm, c->tsd, c->tlip,
-                                                                 n_f, c->phi, c->rec, phi, parent, alpha, c->ctl);
+        k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>((int)c->n_v, n_tot, c->n_t, c->xyz, c->tets, c->tm,
+                                                                 c->tsd, c->tlip, n_f, c->phi, c->rec, phi, parent,
+                                                                 alpha, c->ctl);
     time_end(c, 1);
     c->launches++;
     return cudaGetLastError();

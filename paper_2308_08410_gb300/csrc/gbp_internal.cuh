@@ -479,6 +479,10 @@ struct gbp_ctx {
     int num_sms = 0;
     int64_t n_v = 0, n_t = 0;
     int max_deg = 0;  // max vertex->tet degree
+    // Batch of independent problems on the same mesh (multi-start): every
+    // per-problem array below holds nb_cap problems back to back ([b][n_v] or
+    // [b][n_t]); the kernels of a call run nb of them.
+    int nb = 1, nb_cap = 1;
     // mesh
     float4 *xyz = nullptr;
     int4 *tets = nullptr;

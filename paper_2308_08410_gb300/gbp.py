@@ -91,6 +91,8 @@ def load():
                                   P, P], i32),
         "gbp_forward_backward_host": ([P, C.POINTER(SolveOpts), C.POINTER(Template), i32, P, P, P, P, P, P,
                                        P, P, P], i32),
+        "gbp_forward_backward_batch": ([P, i32, C.POINTER(SolveOpts), C.POINTER(Template), i32, P, P, P, P, P,
+                                        P, P, P, P, P], i32),
         "gbp_local_solve_batch": ([P, i64, P, P, P, P, P, i32, i32, P, P], i32),
         "gbp_enable_timing": ([P, i32], i32),
         "gbp_get_kernel_times": ([P, i32, P, P], i32),
@@ -126,7 +128,7 @@ def exported_symbols():
         "gbp_upload_mesh", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
         "gbp_set_onsets", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
-        "gbp_forward_backward_host", "gbp_local_solve_batch", "gbp_enable_timing",
+        "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_local_solve_batch", "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
         "gbp_ecg_forward_noalloc", "gbp_enable_trace", "gbp_get_trace",
         "gbp_nn_gemm_bf16", "gbp_nn_im2col", "gbp_nn_im2col_t", "gbp_nn_col2im", "gbp_nn_bias_act",
@@ -291,6 +293,26 @@ class Context:
                                              _ptr(ct), _ptr(t), _ptr(target), _ptr(out["loss"]),
                                              _ptr(out.get("ecg")), _ptr(out["d_cf"]), _ptr(out["d_ct"]),
                                              _ptr(out["d_t"]), _ptr(out["d_x"])), "gbp_forward_backward")
+        return out
+
+    def forward_backward_batch(self, cf, ct, target, tmpl, t=None, opts=None, precision=PREC_FP32, out=None):
+        """B evaluations in one pass: cf, ct [B, n_t]; target [B, N, T];
+        t [B, K] or None.  Returns dict of device tensors with a leading B."""
+        import torch
+        B = int(cf.shape[0])
+        dev = self.torch_device
+        if out is None:
+            f32 = dict(dtype=torch.float32, device=dev)
+            out = dict(loss=torch.empty(B, **f32), ecg=torch.empty(B, self.N, tmpl.T, **f32),
+                       d_cf=torch.empty(B, self.n_t, **f32), d_ct=torch.empty(B, self.n_t, **f32),
+                       d_t=torch.empty(B, self.K, **f32), d_x=torch.empty(B, self.K, 3, **f32))
+        tm = make_template(tmpl)
+        o = opts if opts is not None else make_opts()
+        _check(self.lib.gbp_forward_backward_batch(self.h, B, C.byref(o), C.byref(tm), int(precision), _ptr(cf),
+                                                   _ptr(ct), _ptr(t), _ptr(target), _ptr(out["loss"]),
+                                                   _ptr(out.get("ecg")), _ptr(out["d_cf"]), _ptr(out["d_ct"]),
+                                                   _ptr(out["d_t"]), _ptr(out["d_x"])),
+               "gbp_forward_backward_batch")
         return out
 
     def forward_backward_host(self, cf: np.ndarray, ct: np.ndarray, target: np.ndarray, tmpl,
