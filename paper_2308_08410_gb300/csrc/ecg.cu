@@ -15,22 +15,30 @@ namespace gbp {
 constexpr int ECG_NL = 16;   // max leads
 constexpr int ECG_CH = 256;  // vertices staged per chunk
 
-__device__ __forceinline__ float logistic(float z) { return __fdividef(1.f, 1.f + __expf(-z)); }
+// The accurate expf and an IEEE division: the ECG is a sum of up to 10^6
+// terms that can cancel by several orders of magnitude (lead-field rows sum
+// to zero), so the relative error of each sigma carries over multiplied by
+// that condition number; the __expf intrinsic's error grows with |z| (tens
+// of ulp at the |z| ~ 50 this sum still sees).
+__device__ __forceinline__ float logistic(float z) { return 1.f / (1.f + expf(-z)); }
 
 // Per CTA: a contiguous vertex range; thread (s_loc, g) accumulates sample
 // s = s_base + s_loc over the vertices q = g mod G of each staged chunk.
 // Writes part[cta][l][s] (deterministic second-stage reduction).  NL is the
 // number of leads, a compile-time constant so the accumulators stay in
-// registers.
+// registers.  Each chunk of ECG_CH vertices is summed in FP32 and the chunk
+// sums in FP64: the terms of one lead can cancel by orders of magnitude
+// (its lead-field row sums to zero), and a long FP32 running sum would
+// carry its rounding times that cancellation into the result.
 template <int NL>
 __global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const float *__restrict__ L,
                                                    const float *__restrict__ phi, float t0, float dt, float c4,
-                                                   int T_tile, int G, int64_t per_cta, float *__restrict__ part)
+                                                   int T_tile, int G, int64_t per_cta, double *__restrict__ part)
 {
-    extern __shared__ float sm[];
-    float *sphi = sm;               // [ECG_CH]
-    float *sL = sm + ECG_CH;        // [ECG_CH][NL] (vertex-major: one float4 row per vertex)
-    float *red = sL + NL * ECG_CH;  // [G][NL][T_tile]
+    extern __shared__ double smd[];
+    double *red = smd;                                        // [G][NL][T_tile]
+    float *sphi = reinterpret_cast<float *>(red + (size_t)G * NL * T_tile);  // [ECG_CH]
+    float *sL = sphi + ECG_CH;                                // [ECG_CH][NL]
     const int tid = threadIdx.x;
     const int s_loc = tid % T_tile;
     const int g = tid / T_tile;
@@ -39,9 +47,9 @@ __global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const flo
     for (int s_base = 0; s_base < T; s_base += T_tile) {
         const int s = s_base + s_loc;
         const float ts = fmaf((float)s, dt, t0);
-        float acc[NL];
+        double accd[NL];
 #pragma unroll
-        for (int l = 0; l < NL; ++l) acc[l] = 0.f;
+        for (int l = 0; l < NL; ++l) accd[l] = 0.0;
         for (int64_t c0 = n0; c0 < n1; c0 += ECG_CH) {
             const int cnt = (int)min((int64_t)ECG_CH, n1 - c0);
             __syncthreads();
@@ -52,22 +60,27 @@ __global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const flo
             }
             __syncthreads();
             if (s < T) {
+                float acc[NL];
+#pragma unroll
+                for (int l = 0; l < NL; ++l) acc[l] = 0.f;
                 for (int q = g; q < cnt; q += G) {
                     const float sg = logistic((ts - sphi[q]) * c4);
                     const float *Lq = sL + q * NL;
 #pragma unroll
                     for (int l = 0; l < NL; ++l) acc[l] = fmaf(Lq[l], sg, acc[l]);
                 }
+#pragma unroll
+                for (int l = 0; l < NL; ++l) accd[l] += (double)acc[l];
             }
         }
         __syncthreads();
 #pragma unroll
-        for (int l = 0; l < NL; ++l) red[(g * NL + l) * T_tile + s_loc] = acc[l];
+        for (int l = 0; l < NL; ++l) red[(g * NL + l) * T_tile + s_loc] = accd[l];
         __syncthreads();
         for (int e = tid; e < NL * T_tile; e += blockDim.x) {
             const int l = e / T_tile, sl = e - l * T_tile;
             if (s_base + sl >= T) continue;
-            float v = 0.f;
+            double v = 0.0;
             for (int gg = 0; gg < G; ++gg) v += red[(gg * NL + l) * T_tile + sl];
             part[((int64_t)blockIdx.x * NL + l) * T + s_base + sl] = v;
         }
@@ -77,7 +90,7 @@ __global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const flo
 template <int NL>
 static cudaError_t launch_fwd_n(int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
-                                int64_t per, float *part)
+                                int64_t per, double *part)
 {
     cudaFuncSetAttribute(k_ecg_fwd_t<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_ecg_fwd_t<NL><<<ncta, threads, smem, st>>>(n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part);
@@ -87,7 +100,7 @@ static cudaError_t launch_fwd_n(int ncta, int threads, size_t smem, cudaStream_t
 // one instantiation per lead count 1..16
 cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
                                  const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
-                                 int64_t per, float *part)
+                                 int64_t per, double *part)
 {
     switch (N) {
 #define GBP_ECG_CASE(n) \
@@ -100,16 +113,23 @@ cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cuda
     return cudaErrorInvalidValue;
 }
 
-// V[l][s] = K0 S_l + (K1 - K0) sum_cta part[cta][l][s]  (fixed order)
-__global__ void k_ecg_reduce(int N, int T, int ncta, const float *__restrict__ part, const float *__restrict__ rowsum,
+// V[l][s] = K0 S_l + (K1 - K0) sum_cta part[cta][l][s]  (fixed order, FP64)
+__global__ void k_ecg_reduce(int N, int T, int ncta, const double *__restrict__ part, const float *__restrict__ rowsum,
                              float K0, float dK, float *__restrict__ ecg)
 {
     int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N * T) return;
     int l = e / T;
-    float v = 0.f;
+    double v = 0.0;
     for (int c = 0; c < ncta; ++c) v += part[(int64_t)c * N * T + e];
-    ecg[e] = fmaf(K0, rowsum[l], dK * v);
+    ecg[e] = (float)((double)K0 * rowsum[l] + (double)dK * v);
+}
+
+// staging of the FP32 forward: FP64 partials of [ncta][N][T] plus the staged
+// chunk, in bytes of dynamic shared memory
+size_t ecg_fwd_smem(int N, int T_tile, int G)
+{
+    return sizeof(double) * (size_t)G * N * T_tile + sizeof(float) * (ECG_CH + (size_t)N * ECG_CH);
 }
 
 static void ecg_fwd_shape(int T, int *T_tile, int *G)
@@ -131,7 +151,7 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
     int64_t per = (c->n_v + ncta - 1) / ncta;
     per = ((per + ECG_CH - 1) / ECG_CH) * ECG_CH;
     ncta = (int)((c->n_v + per - 1) / per);
-    int64_t need = (int64_t)ncta * N * T;
+    int64_t need = 2 * (int64_t)ncta * N * T;  // FP64 partials, counted in floats
     if (need > c->ecg_part_cap) {
         if (c->ecg_part) cudaFree(c->ecg_part);
         cudaError_t err = cudaMalloc(&c->ecg_part, sizeof(float) * need);
@@ -142,14 +162,15 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
         }
         c->ecg_part_cap = need;
     }
-    size_t smem = sizeof(float) * (ECG_CH + (size_t)N * ECG_CH + (size_t)G * N * T_tile);
+    double *part = reinterpret_cast<double *>(c->ecg_part);
+    size_t smem = ecg_fwd_smem(N, T_tile, G);
     float c4 = 4.f / t->tau;
     time_begin(c, 2);
     cudaError_t le = launch_ecg_fwd_leads(N, ncta, T_tile * G, smem, c->stream, c->n_v, T, c->L, phi, t->t0, t->dt,
-                                          c4, T_tile, G, per, c->ecg_part);
+                                          c4, T_tile, G, per, part);
     if (le) return le;
-    k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, c->stream>>>(N, T, ncta, c->ecg_part, c->Lrowsum, t->K0,
-                                                            t->K1 - t->K0, ecg);
+    k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, c->stream>>>(N, T, ncta, part, c->Lrowsum, t->K0, t->K1 - t->K0,
+                                                            ecg);
     time_end(c, 2);
     c->launches += 2;
     return cudaGetLastError();
@@ -214,8 +235,8 @@ __global__ void __launch_bounds__(256) k_ecg_bwd_t(int64_t n_v, int T, const flo
     float acc = 0.f;
     for (int s = s_lo; s <= s_hi; ++s) {
         const float z = (fmaf((float)s, dt, t0) - p) * c4;
-        const float e = __expf(-fabsf(z));
-        const float w = __fdividef(e, (1.f + e) * (1.f + e));
+        const float e = expf(-fabsf(z));
+        const float w = e / ((1.f + e) * (1.f + e));
         const float *rs = rT + s * NL;
         float cs = 0.f;
 #pragma unroll

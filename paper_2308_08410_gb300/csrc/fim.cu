@@ -222,7 +222,7 @@ struct FimArgs {
 #define GBP_FIM_G 8  // lanes per active vertex
 #endif
 #ifndef GBP_FIM_R
-#define GBP_FIM_R 2  // faces per lane fetched together
+#define GBP_FIM_R 1  // faces per lane fetched together
 #endif
 #ifndef GBP_FIM_DYN
 #define GBP_FIM_DYN 0  // warps fetch active vertices from a counter (else a fixed stride)
@@ -234,7 +234,7 @@ constexpr int FIM_G = GBP_FIM_G;
 constexpr int FIM_R = GBP_FIM_R;
 constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
 #ifndef GBP_FIM_MINB
-#define GBP_FIM_MINB 3  // CTAs per SM (80 registers at 256 threads)
+#define GBP_FIM_MINB 4  // CTAs per SM (64 registers at 256 threads)
 #endif
 constexpr int FIM_MINB = GBP_FIM_MINB;
 constexpr int FIM_CAP = 2048;  // per-CTA append buffer (overflow goes straight to global)

@@ -16,14 +16,15 @@ namespace gbp {
 // kernels shared with the context-based path (ecg.cu)
 cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
                                  const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
-                                 int64_t per, float *part);
-__global__ void k_ecg_reduce(int N, int T, int ncta, const float *__restrict__ part, const float *__restrict__ rowsum,
+                                 int64_t per, double *part);
+__global__ void k_ecg_reduce(int N, int T, int ncta, const double *__restrict__ part, const float *__restrict__ rowsum,
                              float K0, float dK, float *__restrict__ ecg);
+size_t ecg_fwd_smem(int N, int T_tile, int G);
 }  // namespace gbp
 
 namespace {
 
-// 4 MiB of scratch per device: 16 row sums, then the partial sums.
+// 4 MiB of scratch per device: 16 row sums, then the FP64 partial sums.
 constexpr int64_t NOALLOC_SCRATCH_FLOATS = (int64_t)1 << 20;
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
 
@@ -76,7 +77,7 @@ extern "C" gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t
     if (!L || !phi || !ecg || !tmpl || N < 1 || N > 16 || n_v < 1) return GBP_ERR_INVALID_ARG;
     if (tmpl->T < 1 || tmpl->T > 4096 || !(tmpl->tau > 0.f) || !(tmpl->dt > 0.f)) return GBP_ERR_INVALID_ARG;
     const int T = tmpl->T;
-    const int64_t per_cta_floats = (int64_t)N * T;
+    const int64_t per_cta_floats = 2 * (int64_t)N * T;  // FP64 partials
     // the scratch must hold the row sums and at least one CTA's partials
     if (16 + per_cta_floats > NOALLOC_SCRATCH_FLOATS) return GBP_ERR_INVALID_ARG;
     int dev = -1;
@@ -86,7 +87,7 @@ extern "C" gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t
     if (scratch_for_device(dev, &scratch, &sms) != cudaSuccess) return GBP_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
     float *rowsum = scratch;
-    float *part = scratch + 16;
+    double *part = reinterpret_cast<double *>(scratch + 16);  // 64-byte offset: 8-byte aligned
     // same launch shape as the context path, with the CTA count capped by
     // the scratch size
     int tt = ((T + 31) / 32) * 32;
@@ -102,7 +103,7 @@ extern "C" gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t
     ncta = (n_v + per - 1) / per;
     // every partial and row sum is overwritten below, so nothing is cleared
     k_rowsum_noalloc<<<N, 256, 0, st>>>(n_v, L, rowsum);
-    size_t smem = sizeof(float) * (CH + (size_t)N * CH + (size_t)G * N * tt);
+    size_t smem = gbp::ecg_fwd_smem(N, tt, G);
     if (gbp::launch_ecg_fwd_leads(N, (int)ncta, tt * G, smem, st, n_v, T, L, phi, tmpl->t0, tmpl->dt,
                                   4.f / tmpl->tau, tt, G, per, part) != cudaSuccess)
         return GBP_ERR_CUDA;
