@@ -45,7 +45,7 @@ class InverseProblem:
     for a seeded problem uploaded to a context."""
 
     def __init__(self, ctx: gbp.Context, problem, target: np.ndarray, opts=None, precision=gbp.PREC_FP32,
-                 init_log_cf=None, init_log_ct=None, init_t=None, optimise_positions=True):
+                 init_log_cf=None, init_log_ct=None, init_t=None, optimise_positions=True, relocate=True):
         self.ctx = ctx
         self.p = problem
         dev = ctx.torch_device
@@ -70,6 +70,10 @@ class InverseProblem:
         else:
             self.Vt_inv = None
             self.x = torch.zeros(ons.K, 3, device=dev)
+        self.locator = None
+        if self.optimise_positions and relocate:
+            from .relocate import TetLocator
+            self.locator = TetLocator(problem.mesh.xyz, problem.mesh.tets)
         self.op = EvalOp(ctx=ctx, kind=ons.kind, on_idx=self.dp.on_idx,
                          target=torch.from_numpy(np.ascontiguousarray(target, np.float32)).to(dev),
                          tmpl=problem.tmpl, opts=opts if opts is not None else gbp.make_opts(),
@@ -101,14 +105,18 @@ class InverseProblem:
 
     @torch.no_grad()
     def project_positions(self, floor=1e-3):
-        """Keep every onset inside its tet: clamp its barycentric coordinates
-        to >= floor and renormalise (relocation across elements is not
-        modelled)."""
+        """Keep every onset inside the mesh: with relocation, an onset that left
+        its tet moves to the tet that now contains it (relocate.py); without,
+        its barycentric coordinates are clamped to >= floor in its own tet."""
         if self.Vt_inv is None:
+            return
+        if self.locator is not None:
+            from .relocate import relocate_onsets
+            relocate_onsets(self.locator, self.x, self.op.on_idx, self.Vt_inv, floor=floor)
             return
         b = self.bary().clamp_min(floor)
         b = b / b.sum(dim=1, keepdim=True)
-        V = torch.from_numpy(self.p.mesh.xyz.astype(np.float32)).to(self.x.device)[self.tets[self.dp.on_idx.long()]]
+        V = torch.from_numpy(self.p.mesh.xyz.astype(np.float32)).to(self.x.device)[self.tets[self.op.on_idx.long()]]
         self.x.copy_(torch.einsum("kq,kqr->kr", b, V))
 
     def run_adam(self, iters=500, lr=1e-2, log_every=0, callback=None):

@@ -523,7 +523,7 @@ class C5Inverse:
     tets) with the loss and gradient of the C ABI (GeodesicEcgLoss)."""
 
     def __init__(self, dev_c5: C5Device, target_ecg: np.ndarray, init: Params, precision=gbp.PREC_FP32,
-                 opts=None):
+                 opts=None, locator=None):
         from .inverse import EvalOp
         self.d = dev_c5
         ctx = dev_c5.ctx
@@ -539,13 +539,15 @@ class C5Inverse:
         self.Vt = torch.tensor(V, dtype=torch.float32, device=dv)
         self.x = torch.tensor(x0.astype(np.float32), device=dv, requires_grad=True)
         n_v = c5.problem.mesh.n_v
-        self.op = EvalOp(ctx=ctx, kind=gbp.ONSET_ELEMENT, on_idx=torch.from_numpy(init.tet).to(dv),
+        self.op = EvalOp(ctx=ctx, kind=gbp.ONSET_ELEMENT,
+                         on_idx=torch.from_numpy(np.asarray(init.tet, np.int32)).to(dv),
                          target=torch.from_numpy(np.ascontiguousarray(target_ecg, np.float32)).to(dv),
                          tmpl=c5.problem.tmpl, opts=opts if opts is not None else gbp.make_opts(),
                          precision=precision, phi=torch.empty(n_v, device=dv),
                          parent=torch.empty(n_v, dtype=torch.int32, device=dv),
                          alpha=torch.empty(n_v, 3, device=dv),
                          ecg=torch.empty(c5.problem.L.shape[0], c5.problem.tmpl.T, device=dv))
+        self.locator = locator
 
     def bary(self):
         xh = torch.cat([self.x.detach(), torch.ones_like(self.x[:, :1])], dim=1)
@@ -559,6 +561,12 @@ class C5Inverse:
 
     @torch.no_grad()
     def project(self, floor=1e-3):
+        """Onsets that left their tet move to the tet containing them (with a
+        locator, relocate.py); otherwise they are clamped into their tet."""
+        if self.locator is not None:
+            from .relocate import relocate_onsets
+            relocate_onsets(self.locator, self.x, self.op.on_idx, self.Vt_inv, self.Vt, floor=floor)
+            return
         b = self.bary().clamp_min(floor)
         b = b / b.sum(dim=1, keepdim=True)
         self.x.copy_(torch.einsum("kq,kqr->kr", b, self.Vt))
@@ -590,7 +598,7 @@ class C5Inverse:
 # ---------------------------------------------------------------------------
 
 def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, lr_refine=2e-2, seed=0,
-                   noise=0.05, lr_train=2e-3, log=print):
+                   noise=0.05, lr_train=2e-3, relocate=True, log=print):
     """Generate the data with the forward model, train the network, then for
     n_eval held-out noisy ECGs run (a) plain Geodesic-BP from the default
     start with the FP32 ECG and (b) Geodesic-BP from the network's prediction
@@ -609,6 +617,10 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
                           log=lambda h: log(f"epoch {h[0]} train {h[1]:.4e} val {h[2]:.4e} {h[3]:.1f}s"))
     t_train = hist[-1][3]
     rng = np.random.default_rng(seed + 3)
+    loc = None
+    if relocate:
+        from .relocate import TetLocator
+        loc = TetLocator(c5.problem.mesh.xyz, c5.problem.mesh.tets)
     rows = []
     for i in range(n_eval):
         truth = Pv[i]
@@ -616,7 +628,7 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
         phi_true = d.phi.cpu().numpy().copy()
         target = S.add_noise(clean, noise, seed + 100 + i)
         # (a) plain
-        inv_p = C5Inverse(d, target, default_params(c5, rng), precision=gbp.PREC_FP32)
+        inv_p = C5Inverse(d, target, default_params(c5, rng), precision=gbp.PREC_FP32, locator=loc)
         hp = inv_p.run(iters, lr=lr_refine)
         best = min(range(len(hp)), key=lambda k: hp[k][1])
         m_plain, t_plain = hp[best][1], hp[best][2]
@@ -627,7 +639,7 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
         xin = np.ascontiguousarray(target.T[None].astype(np.float32))
         init = decode(c5, predict(net, xin, xs)[0])
         t_inf = time.perf_counter() - ti
-        inv_l = C5Inverse(d, target, init, precision=gbp.PREC_BF16)
+        inv_l = C5Inverse(d, target, init, precision=gbp.PREC_BF16, locator=loc)
         hl = inv_l.run(iters, lr=lr_refine, stop_at=m_plain)
         reached = [h for h in hl if h[1] <= m_plain]
         t_learned = (reached[0][2] if reached else float("inf")) + t_inf
@@ -638,7 +650,7 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
                          learned_final=hl[-1][1], plain_rmse=rmse(phi_p), learned_rmse=rmse(phi_l)))
         log(rows[-1])
     med = lambda k: float(np.median([r[k] for r in rows]))  # noqa: E731
-    return dict(n_train=n_train, n_test=n_test, epochs=epochs, gen_s=t_gen, train_s=t_train,
+    return dict(n_train=n_train, n_test=n_test, epochs=epochs, gen_s=t_gen, train_s=t_train, relocate=relocate,
                 val_mse=float(hist[-1][2]), cases=rows,
                 median=dict(plain_time=med("plain_time"), learned_time=med("learned_time"),
                             plain_loss0=med("plain_loss0"), learned_loss0=med("learned_loss0"),
@@ -657,8 +669,9 @@ if __name__ == "__main__":
     ap.add_argument("--eval", type=int, default=20)
     ap.add_argument("--iters", type=int, default=300)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--no-relocate", action="store_true", help="keep every onset inside its initial tet")
     a = ap.parse_args()
-    res = run_experiment(a.train, a.test, a.epochs, a.eval, a.iters)
+    res = run_experiment(a.train, a.test, a.epochs, a.eval, a.iters, relocate=not a.no_relocate)
     s = json.dumps(res)
     print(s)
     if a.out:
