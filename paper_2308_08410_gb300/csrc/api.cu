@@ -58,6 +58,8 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->n2t);
     dfree(&c->n2n_ptr);
     dfree(&c->n2n);
+    dfree(&c->frec);
+    dfree(&c->pc);
     dfree(&c->fib);
     dfree(&c->cf);
     dfree(&c->ct);
@@ -318,6 +320,8 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     CK(dalloc(&c->n2t, 4 * n_t));
     CK(dalloc(&c->n2n_ptr, n_v + 1));
     CK(dalloc(&c->n2n, (int64_t)n2n.size()));
+    CK(dalloc(&c->frec, 4 * n_t));
+    CK(dalloc(&c->pc, n_v));
     CK(dalloc(&c->fib, 3 * n_t));
     CK(dalloc(&c->cf, n_t));
     CK(dalloc(&c->ct, n_t));
@@ -343,6 +347,20 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     CK(cudaMemcpy(c->n2t, n2t.data(), sizeof(int) * 4 * n_t, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->n2n_ptr, n2n_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->n2n, n2n.data(), sizeof(int) * n2n.size(), cudaMemcpyHostToDevice));
+    {
+        // face records in vertex->tet order: the three other vertices in slot order, code
+        std::vector<int4> fr(4 * n_t);
+        for (int64_t e = 0; e < 4 * n_t; ++e) {
+            const int code = n2t[e];
+            const int64_t j = code >> 2;
+            const int s = code & 3;
+            int f[3], q3 = 0;
+            for (int q = 0; q < 4; ++q)
+                if (q != s) f[q3++] = tets[4 * j + q];
+            fr[e] = make_int4(f[0], f[1], f[2], code);
+        }
+        CK(cudaMemcpy(c->frec, fr.data(), sizeof(int4) * fr.size(), cudaMemcpyHostToDevice));
+    }
 #undef CK
     if (err) {
         free_mesh_buffers(c);
@@ -641,6 +659,7 @@ static cudaError_t ensure_batch(gbp_ctx *c, int B)
     CK(dalloc(&c->adj_w, nv));
     CK(dalloc(&c->proc, nv));
     CK(dalloc(&c->dphi, nv));
+    CK(dalloc(&c->pc, nv));
     if (c->K) CK(dalloc(&c->on_t, (int64_t)c->K * B));
 #undef CK
     c->has_vel = false;

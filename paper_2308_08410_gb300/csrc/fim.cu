@@ -5,6 +5,36 @@
 
 namespace gbp {
 
+// Vertex state written during the solve is read through L2 only (values of
+// other SMs from earlier iterations; same-iteration values may be stale,
+// which the chaotic relaxation of Algorithm 2 tolerates).
+#define FIM_LD(p) __ldcg(p)
+
+// vertices of the face of tet tv opposite slot s, in increasing slot order
+__device__ __forceinline__ void face_ids(int4 tv, int s, int &vi, int &f0, int &f1, int &f2)
+{
+    vi = s == 0 ? tv.x : s == 1 ? tv.y : s == 2 ? tv.z : tv.w;
+    f0 = s == 0 ? tv.y : tv.x;
+    f1 = s <= 1 ? tv.z : tv.y;
+    f2 = s <= 2 ? tv.w : tv.z;
+}
+
+// transformed edge vectors p_n = R (v_{j_n} - v_i) of face (tet tv, opposite slot s)
+__device__ __forceinline__ void face_vectors(const float4 *__restrict__ xyz, int4 tv, int s, float4 m, float sd,
+                                             float3 p[3], int fv[3])
+{
+    int vi, f0, f1, f2;
+    face_ids(tv, s, vi, f0, f1, f2);
+    fv[0] = f0;
+    fv[1] = f1;
+    fv[2] = f2;
+    const float4 xi = __ldg(&xyz[vi]);
+    const float4 x0 = __ldg(&xyz[f0]), x1 = __ldg(&xyz[f1]), x2 = __ldg(&xyz[f2]);
+    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
+    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
+    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
+}
+
 // ---------------------------------------------------------------------------
 // per-tet metric (Sec. II-A): R = D^{1/2} in factored form
 // ---------------------------------------------------------------------------
@@ -39,31 +69,6 @@ cudaError_t launch_precompute(gbp_ctx *c)
     k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->fib, c->cf, c->ct, c->tm, c->tsd, c->ctl);
     c->launches++;
     return cudaGetLastError();
-}
-
-// vertices of the face of tet tv opposite slot s, in increasing slot order
-__device__ __forceinline__ void face_ids(int4 tv, int s, int &vi, int &f0, int &f1, int &f2)
-{
-    vi = s == 0 ? tv.x : s == 1 ? tv.y : s == 2 ? tv.z : tv.w;
-    f0 = s == 0 ? tv.y : tv.x;
-    f1 = s <= 1 ? tv.z : tv.y;
-    f2 = s <= 2 ? tv.w : tv.z;
-}
-
-// transformed edge vectors p_n = R (v_{j_n} - v_i) of face (tet tv, opposite slot s)
-__device__ __forceinline__ void face_vectors(const float4 *__restrict__ xyz, int4 tv, int s, float4 m, float sd,
-                                             float3 p[3], int fv[3])
-{
-    int vi, f0, f1, f2;
-    face_ids(tv, s, vi, f0, f1, f2);
-    fv[0] = f0;
-    fv[1] = f1;
-    fv[2] = f2;
-    const float4 xi = __ldg(&xyz[vi]);
-    const float4 x0 = __ldg(&xyz[f0]), x1 = __ldg(&xyz[f1]), x2 = __ldg(&xyz[f2]);
-    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
-    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
-    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
 }
 
 __global__ void k_lipschitz(int64_t n_t, int64_t n_tot, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
@@ -149,7 +154,7 @@ __global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ id
 
 // Per vertex: decode the onset key, reset the FIM state.
 __global__ void k_init_nodes(int64_t n_v, const unsigned long long *__restrict__ keys, float *phi, int4 *rec,
-                             int *chg, int *stamp)
+                             int *chg, int *stamp, int2 *pc)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_v) return;
@@ -164,6 +169,14 @@ __global__ void k_init_nodes(int64_t n_v, const unsigned long long *__restrict__
         chg[i] = -1000000;
     }
     stamp[i] = 0;
+    pc[i] = make_int2(__float_as_int(phi[i]), chg[i]);
+}
+
+// phi of every vertex entry from the FIM's packed (value, change stamp) state
+__global__ void k_unpack_pc(int64_t n_tot, const int2 *__restrict__ pc, float *phi)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g < n_tot) phi[g] = __int_as_float(pc[g].x);
 }
 
 // Seeded vertices put their neighbours on the first active list.
@@ -197,6 +210,8 @@ struct FimArgs {
     const float *tsd;
     const float4 *tlip;
     const int *n2t_ptr, *n2t, *n2n_ptr, *n2n;
+    const int4 *frec;   // per vertex->tet entry: face vertex ids (slot order) and tet*4 + slot
+    int2 *pc;           // per vertex entry: (value bits, iteration of the last change)
     float *phi;
     int4 *rec;
     int *chg, *stamp, *lists;
@@ -209,10 +224,12 @@ struct FimArgs {
 
 // One iteration k = one Jacobi-style sweep of Algorithm 2 restricted to the
 // active vertices (neighbours of the vertices that changed at k-1).  A group
-// of FIM_G lanes owns one active vertex i: its lanes take i's incident tets
-// from the vertex->tet adjacency, solve the local problem of every face
-// E_{j\i} that has a vertex changed since k-1 (the optional mask of
-// Algorithm 2) and reduce the minimum (Eq. hopflax_global).  A vertex that
+// of FIM_G lanes owns one active vertex i: its lanes take i's face records
+// (the three other vertices of an incident tet and the code tet*4 + slot, in
+// vertex->tet order), read each face vertex's packed (value, change stamp),
+// solve the local problem of every face E_{j\i} that has a vertex changed
+// since k-1 (the optional mask of Algorithm 2) and reduce the minimum
+// (Eq. hopflax_global).  A vertex that
 // decreased by more than eps is marked changed and activates its neighbours
 // for k+1 (appended through a per-CTA shared-memory buffer, one global
 // atomic per CTA and iteration).  Reads of neighbour values may see this
@@ -295,7 +312,7 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             if (!__any_sync(0xffffffffu, act)) break;
 #endif
             // entry gi = b * n_v + i: vertex i of problem b
-            int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0;
+            int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0, chg_old = 0;
             int64_t toff = 0;
             float phi_old = 0.f;
             float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -305,7 +322,9 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
                 boff = b * (int)n_v;
                 toff = (int64_t)b * a.n_t;
                 i = gi - boff;
-                phi_old = __ldcg(&a.phi[gi]);
+                const int2 own = FIM_LD(&a.pc[gi]);
+                phi_old = __int_as_float(own.x);
+                chg_old = own.y;
                 beg = __ldg(&a.n2t_ptr[i]);
                 end = __ldg(&a.n2t_ptr[i + 1]);
                 nb = __ldg(&a.n2n_ptr[i]);
@@ -319,44 +338,39 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             // values are fetched together (three dependent loads for all of
             // them), then the masked ones are solved
             for (int e0 = 0; e0 < maxdeg; e0 += FIM_G * FIM_R) {
-                int code[FIM_R];
+                // the face record (face vertex ids, code), then each face
+                // vertex's packed value and change stamp
+                int4 fr[FIM_R];
 #pragma unroll
                 for (int r = 0; r < FIM_R; ++r) {
                     const int e = beg + e0 + r * FIM_G + sub;
-                    code[r] = e < end ? __ldg(&a.n2t[e]) : -1;
+                    fr[r] = e < end ? __ldg(&a.frec[e]) : make_int4(0, 0, 0, -1);
                 }
-                int4 tv[FIM_R];
-#pragma unroll
-                for (int r = 0; r < FIM_R; ++r)
-                    tv[r] = code[r] >= 0 ? __ldg(&a.tets[code[r] >> 2]) : make_int4(0, 0, 0, 0);
                 float ph[FIM_R][3];
                 bool mk[FIM_R];
 #pragma unroll
                 for (int r = 0; r < FIM_R; ++r) {
                     mk[r] = false;
                     ph[r][0] = ph[r][1] = ph[r][2] = GBP_INF;
-                    if (code[r] >= 0) {
-                        int vi, f0, f1, f2;
-                        face_ids(tv[r], code[r] & 3, vi, f0, f1, f2);
-                        const int c0 = __ldcg(&a.chg[boff + f0]), c1 = __ldcg(&a.chg[boff + f1]),
-                                  c2 = __ldcg(&a.chg[boff + f2]);
-                        ph[r][0] = __ldcg(&a.phi[boff + f0]);
-                        ph[r][1] = __ldcg(&a.phi[boff + f1]);
-                        ph[r][2] = __ldcg(&a.phi[boff + f2]);
-                        mk[r] = max(c0, max(c1, c2)) >= k - 1;
+                    if (fr[r].w >= 0) {
+                        const int2 q0 = FIM_LD(&a.pc[boff + fr[r].x]), q1 = FIM_LD(&a.pc[boff + fr[r].y]),
+                                   q2 = FIM_LD(&a.pc[boff + fr[r].z]);
+                        ph[r][0] = __int_as_float(q0.x);
+                        ph[r][1] = __int_as_float(q1.x);
+                        ph[r][2] = __int_as_float(q2.x);
+                        mk[r] = max(q0.y, max(q1.y, q2.y)) >= k - 1;
                     }
                 }
 #pragma unroll
                 for (int r = 0; r < FIM_R; ++r) {
                     if (!mk[r]) continue;
-                    ++my_faces;
-                    const int code_r = code[r];
+                    const int code_r = fr[r].w;
                     const int j = code_r >> 2, s = code_r & 3;
+                    ++my_faces;
                     const float4 m = __ldg(&a.tm[toff + j]);
                     const float sd = __ldg(&a.tsd[toff + j]);
-                    int vi, f0, f1, f2;
-                    face_ids(tv[r], s, vi, f0, f1, f2);
-                    const float4 x0 = __ldg(&a.xyz[f0]), x1 = __ldg(&a.xyz[f1]), x2 = __ldg(&a.xyz[f2]);
+                    const float4 x0 = __ldg(&a.xyz[fr[r].x]), x1 = __ldg(&a.xyz[fr[r].y]),
+                                 x2 = __ldg(&a.xyz[fr[r].z]);
                     float3 p[3];
                     p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
                     p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
@@ -389,9 +403,9 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             if (act && best < phi_old) {
                 changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
                 if (sub == 0) {
-                    a.phi[gi] = best;
+                    // value and change stamp in one 8-byte store: readers see a pair
+                    a.pc[gi] = make_int2(__float_as_int(best), changed ? k : chg_old);
                     a.rec[gi].x = best_code;
-                    if (changed) a.chg[gi] = k;
                 }
             }
             // activate the neighbours of changed vertices for iteration k+1
@@ -474,7 +488,7 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
                                                                       c->on_bary, c->on_t, n_v, c->n_t, c->xyz,
                                                                       c->tets, c->tm, c->tsd, c->keys, c->ctl);
     unsigned bl = (unsigned)((n_tot + th - 1) / th);
-    k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp);
+    k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp, c->pc);
     c->launches += 2;
     if ((err = cudaGetLastError())) return err;
     long long *trace = nullptr;
@@ -505,6 +519,8 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     a.tm = c->tm;
     a.tsd = c->tsd;
     a.tlip = c->tlip;
+    a.frec = c->frec;
+    a.pc = c->pc;
     a.n2t_ptr = c->n2t_ptr;
     a.n2t = c->n2t;
     a.n2n_ptr = c->n2n_ptr;
@@ -527,7 +543,10 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(FIM_BLOCK), args, 0, c->stream);
     time_end(c, 0);
     c->launches++;
-    return err;
+    if (err) return err;
+    k_unpack_pc<<<bl, th, 0, c->stream>>>(n_tot, c->pc, c->phi);
+    c->launches++;
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

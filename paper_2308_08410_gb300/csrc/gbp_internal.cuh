@@ -503,7 +503,7 @@ struct gbp_ctx {
     int4 *tets = nullptr;
     int *n2t_ptr = nullptr, *n2t = nullptr;
     int *n2n_ptr = nullptr, *n2n = nullptr;
-    // parameters
+    int4 *frec = nullptr;  // per vertex->tet entry: face vertex ids (slot order), tet*4 + slot
     float *fib = nullptr, *cf = nullptr, *ct = nullptr;
     float4 *tm = nullptr;   // (fx, fy, fz, 1/ct)
     float *tsd = nullptr;   // 1/cf - 1/ct
@@ -524,6 +524,7 @@ struct gbp_ctx {
     float *phi = nullptr;
     int4 *rec = nullptr;  // (parent code, alpha0, alpha1, alpha2 as float bits)
     int *chg = nullptr, *stamp = nullptr, *lists = nullptr;
+    int2 *pc = nullptr;  // FIM state: (value bits, iteration of the last change) per vertex entry
     unsigned long long *keys = nullptr;
     gbp::Control *ctl = nullptr;
     gbp::Control *h_ctl = nullptr;  // pinned
