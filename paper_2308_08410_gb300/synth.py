@@ -32,7 +32,7 @@ import math
 import numpy as np
 
 __all__ = [
-    "Mesh", "Onsets", "Template", "Problem",
+    "Mesh", "Onsets", "Template", "Problem", "TriMesh", "Problem2D", "make_2d",
     "kuhn_cube", "voxel_kuhn", "biv_shell_mask",
     "fibres_cube", "fibres_biv", "smooth_field", "nodal_to_tet_mean",
     "fibonacci_sphere", "torso_electrodes", "lead_field", "twelve_lead_matrix",
@@ -554,3 +554,82 @@ def random_faces(n: int, seed: int, aniso: float = 2.0, spread: float = 4.0,
         phi[m] = np.inf
     return (e.astype(np.float32), f.astype(np.float32), cf.astype(np.float32),
             ct.astype(np.float32), phi.astype(np.float32))
+
+
+# ----------------------------------------------------------------------------
+# 2-D triangle meshes (the paper's d = 2 setting)
+# ----------------------------------------------------------------------------
+@dataclasses.dataclass
+class TriMesh:
+    xy: np.ndarray    # float32 [n_v, 2], mm
+    tris: np.ndarray  # int32 [n_t, 3], counter-clockwise
+
+    @property
+    def n_v(self) -> int:
+        return int(self.xy.shape[0])
+
+    @property
+    def n_t(self) -> int:
+        return int(self.tris.shape[0])
+
+
+@dataclasses.dataclass
+class Problem2D:
+    name: str
+    mesh: TriMesh
+    fib: np.ndarray   # float32 [n_t, 2], unit
+    cf: np.ndarray    # float32 [n_t]
+    ct: np.ndarray    # float32 [n_t]
+    onset_nodes: np.ndarray  # int32 [K]
+    onset_t: np.ndarray      # float32 [K]
+    L: np.ndarray     # float32 [N, n_v]
+    tmpl: Template
+
+
+def tri_square(n: int, side: float = 10.0, jitter: float = 0.0, seed: int = 0) -> TriMesh:
+    """n x n vertex grid on [0, side]^2 split into 2 counter-clockwise
+    triangles per cell (alternating diagonals); interior vertices jittered by
+    up to jitter * h."""
+    h = side / (n - 1)
+    g = np.arange(n)
+    X, Y = np.meshgrid(g, g, indexing="xy")
+    xy = np.stack([X.ravel(), Y.ravel()], axis=1).astype(np.float64) * h
+    if jitter > 0:
+        r = np.random.default_rng(seed)
+        inner = (X.ravel() > 0) & (X.ravel() < n - 1) & (Y.ravel() > 0) & (Y.ravel() < n - 1)
+        xy[inner] += r.uniform(-jitter * h, jitter * h, size=(int(inner.sum()), 2))
+    tris = []
+    for j in range(n - 1):
+        for i in range(n - 1):
+            a, b, c, d = j * n + i, j * n + i + 1, (j + 1) * n + i + 1, (j + 1) * n + i
+            if (i + j) % 2 == 0:
+                tris += [(a, b, c), (a, c, d)]
+            else:
+                tris += [(a, b, d), (b, c, d)]
+    return TriMesh(xy.astype(np.float32), np.asarray(tris, np.int32))
+
+
+def make_2d(n: int = 40, seed: int = 0, side: float = 10.0, n_leads: int = 7, K: int = 2, T: int = 120,
+            jitter: float = 0.25) -> Problem2D:
+    """2-D workload in the spirit of the paper's torso-slice study: a
+    jittered triangulated square, fibres in the plane rotating -60 .. +60 deg
+    across it, c_f = 0.6 / c_t = 0.3 mm/ms with 5 % per-triangle jitter, K
+    nodal onsets with t ~ U[0, 10] ms, n_leads electrodes on a circle of
+    radius 2 * side around the centre with a 1 / r lead field whose rows are
+    centred to sum to zero, T samples at 1 ms."""
+    r = np.random.default_rng(seed)
+    mesh = tri_square(n, side, jitter, seed)
+    cen = mesh.xy.astype(np.float64)[mesh.tris].mean(axis=1)
+    ang = np.deg2rad(-60.0 + 120.0 * cen[:, 1] / side)
+    fib = np.stack([np.cos(ang), np.sin(ang)], axis=1).astype(np.float32)
+    cf = (0.6 * (1 + 0.05 * r.standard_normal(mesh.n_t))).astype(np.float32)
+    ct = (0.3 * (1 + 0.05 * r.standard_normal(mesh.n_t))).astype(np.float32)
+    nodes = r.choice(mesh.n_v, size=K, replace=False).astype(np.int32)
+    t = r.uniform(0.0, 10.0, size=K).astype(np.float32)
+    th = 2 * np.pi * (np.arange(n_leads) + 0.5) / n_leads
+    el = side / 2 + 2 * side * np.stack([np.cos(th), np.sin(th)], axis=1)
+    d = np.linalg.norm(mesh.xy.astype(np.float64)[None, :, :] - el[:, None, :], axis=2)
+    L = 1.0 / d
+    L -= L.mean(axis=1, keepdims=True)
+    L *= 100.0 / mesh.n_v
+    return Problem2D("2d", mesh, fib, cf, ct, nodes, t, L.astype(np.float32), Template(-80.0, 20.0, 1.0, 0.0, 1.0, T))
