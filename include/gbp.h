@@ -126,6 +126,24 @@ gbp_status gbp_synchronize(gbp_ctx *ctx);
 gbp_status gbp_upload_mesh(gbp_ctx *ctx, const float *xyz, int64_t n_v, const int32_t *tets,
                            int64_t n_t);
 
+/* Triangle mesh (d = 2; Sec. II states the method for any d, and in 2-D
+ * the face opposite a vertex is an edge): xy host float32 [n_v][2], tris
+ * host int32 [n_t][3], counter-clockwise.  Validates (ids in range and
+ * distinct, signed area > 0) and sets the context to d = 2, in which the
+ * other calls take their 2-D layouts:
+ *   fibres [n_t][2]; element-onset barycentric coordinates [K][3] over the
+ *   triangle; lead field [N][n_v]; phi, dphi [n_v]; parent code
+ *   = triangle * 3 + slot with alpha [n_v][2], the weights of the
+ *   triangle's other two vertices in slot order; d_x [K][2] (and
+ *   [B][K][2] in the batched call).
+ * Internally each triangle is solved as the tet (a, b, c, apex) with one
+ * apex above the plane that no onset reaches: the face of a vertex then
+ * holds one vertex at +inf and the local minimiser reduces exactly to the
+ * edge problem.  Synchronous.  Errors: GBP_ERR_BAD_MESH, GBP_ERR_INVALID_ARG.
+ * Invalidates what gbp_upload_mesh invalidates. */
+gbp_status gbp_upload_mesh_2d(gbp_ctx *ctx, const float *xy, int64_t n_v, const int32_t *tris,
+                              int64_t n_t);
+
 /* Fibre directions f_j: device float32 [n_t][3] (normalised here; a zero
  * vector is GBP_ERR_NOT_SPD at the next velocity update). Copied. */
 gbp_status gbp_set_fibres(gbp_ctx *ctx, const float *fib);

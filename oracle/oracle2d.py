@@ -77,21 +77,50 @@ class Mesh2D:
                 self.v2t[t[s]].append((j, s))
 
 
-def eikonal(mesh: Mesh2D, fib, cf, ct, onset_nodes, onset_t):
+def onset_values(mesh: Mesh2D, fib, cf, ct, onset_idx, onset_t, onset_bary=None):
+    """Initial values phi^0 (Sec. II, Eq. upwind_xi in 2-D): a nodal onset k
+    (onset_bary None) sets phi^0 = t_k at vertex onset_idx[k]; an element
+    onset at x_k = sum_q b_q v_q inside triangle E = onset_idx[k] sets
+    phi^0_v = t_k + ||v - x_k||_{D_E} at the three vertices of E.  Minimum
+    over onsets; returns (phi0, code) with code -1-k of the winning onset."""
+    phi = np.full(mesh.n_v, np.inf)
+    code = np.full(mesh.n_v, np.iinfo(np.int32).min, np.int64)
+    for k, t in enumerate(onset_t):
+        if onset_bary is None:
+            pairs = [(int(onset_idx[k]), float(t))]
+        else:
+            E = int(onset_idx[k])
+            tri = mesh.tris[E]
+            x = np.asarray(onset_bary[k], np.float64) @ mesh.xy[tri]
+            R = metric_root(fib[E], cf[E], ct[E])
+            pairs = [(int(v), float(t) + np.linalg.norm(R @ (mesh.xy[v] - x))) for v in tri]
+        for v, val in pairs:
+            if val < phi[v]:
+                phi[v], code[v] = val, -1 - k
+    return phi, code
+
+
+def eikonal(mesh: Mesh2D, fib, cf, ct, onset_idx, onset_t, onset_bary=None):
     """Fixed point of phi_i = min(phi_i^0, min over triangles of the local
     problem); parent code = tri * 3 + slot of i, alpha = weights of the two
-    other vertices in slot order.  Nodal onsets (min over onsets)."""
+    other vertices in slot order; onsets as in onset_values."""
     n = mesh.n_v
     R = [metric_root(fib[j], cf[j], ct[j]) for j in range(mesh.n_t)]
-    phi = np.full(n, np.inf)
-    parent = np.full(n, np.iinfo(np.int32).min, np.int64)
+    phi, parent = onset_values(mesh, fib, cf, ct, onset_idx, onset_t, onset_bary)
+    phi0 = phi.copy()
     alpha = np.zeros((n, 2))
-    for k, (v, t) in enumerate(zip(onset_nodes, onset_t)):
-        if t < phi[v]:
-            phi[v] = float(t)
-            parent[v] = -1 - k
-    heap = [(phi[v], v) for v in set(int(v) for v in onset_nodes)]
+    heap = [(phi[v], v) for v in np.nonzero(np.isfinite(phi))[0]]
     heapq.heapify(heap)
+
+    def candidates(i):
+        out = []
+        for j, s in mesh.v2t[i]:
+            t = mesh.tris[j]
+            o = [t[q] for q in range(3) if q != s]
+            v, _ = local_edge(R[j] @ (mesh.xy[o[0]] - mesh.xy[i]), R[j] @ (mesh.xy[o[1]] - mesh.xy[i]),
+                              phi[o[0]], phi[o[1]])
+            out.append(v)
+        return out
 
     def solve_vertex(i):
         best = (phi[i], parent[i], alpha[i].copy())
@@ -121,22 +150,46 @@ def eikonal(mesh: Mesh2D, fib, cf, ct, onset_nodes, onset_t):
                 if val < phi[i] * (1 - 1e-15) - 1e-300:
                     phi[i], parent[i], alpha[i] = val, code, al
                     heapq.heappush(heap, (val, i))
-    # final parent records at the fixed point
+    # final parent records at the fixed point; margin = gap between the
+    # winning value and the next candidate (another triangle, or the onset
+    # value), which tells where the argmin is unambiguous
+    margin = np.full(n, np.inf)
     for i in range(n):
         if parent[i] >= 0:
             val, code, al = solve_vertex(i)
             if code >= 0 and val <= phi[i] * (1 + 1e-12):
                 parent[i], alpha[i] = code, al
-    return dict(phi=phi, parent=parent, alpha=alpha)
+        if np.isfinite(phi[i]):
+            c = sorted(candidates(i) + ([phi0[i]] if np.isfinite(phi0[i]) else []))
+            if len(c) > 1:
+                margin[i] = c[1] - c[0]
+    return dict(phi=phi, parent=parent, alpha=alpha, margin=margin)
 
 
-def adjoint(mesh: Mesh2D, fib, cf, ct, onset_nodes, parent, alpha, lam):
+def _velocity_terms(f, c_f, c_t, w):
+    """(d/dc_f, d/dc_t) of ||w||_D for D = M^{-1}:
+    ||w||_D^2 = |w_perp|^2 / c_t^2 + (f.w)^2 / c_f^2."""
+    f = np.asarray(f, np.float64)
+    f = f / np.linalg.norm(f)
+    fw = f @ w
+    wp = w - fw * f
+    g = np.sqrt(wp @ wp / c_t ** 2 + fw * fw / c_f ** 2)
+    if g == 0:
+        return 0.0, 0.0
+    return -fw * fw / (c_f ** 3 * g), -(wp @ wp) / (c_t ** 3 * g)
+
+
+def adjoint(mesh: Mesh2D, fib, cf, ct, onset_idx, parent, alpha, lam, onset_t=None, onset_bary=None):
     """mu = (I - P^T)^{-1} lam along the frozen parent graph (P[c, n] = alpha of
     parent vertex n in child c's parent edge), then the per-triangle velocity
-    derivatives and the onset-time derivatives (Sec. II-C):
+    derivatives and the onset derivatives (Sec. II-C):
         phi_i = sum_n alpha_n phi_n + ||w||_D,  w = v_i - sum_n alpha_n v_n,
         d phi_i / d c_f = -(f.w)^2 / (c_f^3 ||w||_D),
-        d phi_i / d c_t = -|w_perp|^2 / (c_t^3 ||w||_D)."""
+        d phi_i / d c_t = -|w_perp|^2 / (c_t^3 ||w||_D).
+    An onset root v of onset k adds mu_v to d_t[k]; for an element onset
+    (onset_bary given) phi_v = t_k + ||v - x_k||_{D_E} also adds
+    mu_v * (-D_E (v - x_k) / ||v - x_k||_{D_E}) to d_x[k] and the velocity
+    terms of E with w = v - x_k."""
     n = mesh.n_v
     rows, cols, vals = [], [], []
     for i in range(n):
@@ -161,17 +214,29 @@ def adjoint(mesh: Mesh2D, fib, cf, ct, onset_nodes, parent, alpha, lam):
         j, s = divmod(int(c), 3)
         o = [mesh.tris[j][q] for q in range(3) if q != s]
         w = mesh.xy[i] - alpha[i][0] * mesh.xy[o[0]] - alpha[i][1] * mesh.xy[o[1]]
-        f = np.asarray(fib[j], np.float64)
-        f = f / np.linalg.norm(f)
-        fw = f @ w
-        wp = w - fw * f
-        g = np.sqrt(wp @ wp / ct[j] ** 2 + fw * fw / cf[j] ** 2)
-        if g > 0:
-            d_cf[j] += -mu[i] * fw * fw / (cf[j] ** 3 * g)
-            d_ct[j] += -mu[i] * (wp @ wp) / (ct[j] ** 3 * g)
-    d_t = np.zeros(len(onset_nodes))
+        a_f, a_t = _velocity_terms(fib[j], cf[j], ct[j], w)
+        d_cf[j] += mu[i] * a_f
+        d_ct[j] += mu[i] * a_t
+    K = len(onset_idx)
+    d_t = np.zeros(K)
+    d_x = np.zeros((K, 2))
     for i in range(n):
         c = parent[i]
-        if np.iinfo(np.int32).min < c < 0:
-            d_t[-1 - c] += mu[i]
-    return dict(mu=mu, d_cf=d_cf, d_ct=d_ct, d_t=d_t)
+        if not np.iinfo(np.int32).min < c < 0:
+            continue
+        k = -1 - int(c)
+        d_t[k] += mu[i]
+        if onset_bary is None:
+            continue
+        E = int(onset_idx[k])
+        x = np.asarray(onset_bary[k], np.float64) @ mesh.xy[mesh.tris[E]]
+        w = mesh.xy[i] - x
+        R = metric_root(fib[E], cf[E], ct[E])
+        D = R.T @ R
+        g = np.sqrt(w @ D @ w)
+        if g > 0:
+            d_x[k] += mu[i] * (-(D @ w) / g)
+            a_f, a_t = _velocity_terms(fib[E], cf[E], ct[E], w)
+            d_cf[E] += mu[i] * a_f
+            d_ct[E] += mu[i] * a_t
+    return dict(mu=mu, d_cf=d_cf, d_ct=d_ct, d_t=d_t, d_x=d_x)

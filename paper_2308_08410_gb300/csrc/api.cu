@@ -86,6 +86,8 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->on_bary);
     dfree(&c->on_t);
     dfree(&c->dphi);
+    dfree(&c->dx3);
+    c->dx3_cap = 0;
     c->has_fib = c->has_vel = c->lip_valid = false;
     c->N = 0;
     c->K = 0;
@@ -116,6 +118,25 @@ __global__ void k_rowsum(int64_t n_v, const float *__restrict__ L, float *__rest
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (threadIdx.x == 0) rowsum[blockIdx.x] = (float)v;
     }
+}
+
+// dst[r][q] = src[r][q] for q < sc, 0 beyond (rows of sc floats -> rows of dc)
+__global__ void k_restride(int64_t rows, int sc, const float *__restrict__ src, int dc, float *__restrict__ dst)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= rows * dc) return;
+    const int64_t r = g / dc;
+    const int q = (int)(g - r * dc);
+    dst[g] = q < sc ? src[r * sc + q] : 0.f;
+}
+
+cudaError_t restride(gbp_ctx *c, int64_t rows, int sc, const float *src, int dc, float *dst)
+{
+    const int64_t n = rows * dc;
+    if (n <= 0) return cudaSuccess;
+    k_restride<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(rows, sc, src, dc, dst);
+    c->launches++;
+    return cudaGetLastError();
 }
 
 bool valid_template(const gbp_template *t)
@@ -238,6 +259,9 @@ gbp_status gbp_synchronize(gbp_ctx *c)
     return latched(c);
 }
 
+static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t,
+                             int64_t n_real, int dim);
+
 gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
 {
     if (!c || !xyz || !tets || n_v < 4 || n_t < 1 || n_v >= (1ll << 30) || n_t >= (1ll << 29))
@@ -270,15 +294,29 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
                      e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
         if (!(det / 6.0 > vtol)) return GBP_ERR_BAD_MESH;
     }
+    return build_mesh(c, xyz, n_v, tets, n_t, n_v, 3);
+}
+
+// Adjacency, face records and device buffers of a validated tet mesh.
+// Vertices from n_real on (the apex of a lifted triangle mesh) get an empty
+// vertex->tet row and appear in no vertex->vertex row: they are never solved
+// nor activated.
+static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t,
+                             int64_t n_real, int dim)
+{
     // vertex -> (tet*4 + slot), rows sorted
-    std::vector<int> n2t_ptr(n_v + 1, 0), n2t(4 * n_t);
+    std::vector<int> n2t_ptr(n_v + 1, 0);
     for (int64_t j = 0; j < n_t; ++j)
-        for (int q = 0; q < 4; ++q) n2t_ptr[tets[4 * j + q] + 1]++;
+        for (int q = 0; q < 4; ++q)
+            if (tets[4 * j + q] < n_real) n2t_ptr[tets[4 * j + q] + 1]++;
     for (int64_t i = 0; i < n_v; ++i) n2t_ptr[i + 1] += n2t_ptr[i];
+    const int64_t n_faces = n2t_ptr[n_v];
+    std::vector<int> n2t(n_faces > 0 ? n_faces : 1);
     {
         std::vector<int> cur(n2t_ptr.begin(), n2t_ptr.end() - 1);
         for (int64_t j = 0; j < n_t; ++j)
-            for (int q = 0; q < 4; ++q) n2t[cur[tets[4 * j + q]]++] = (int)(4 * j + q);
+            for (int q = 0; q < 4; ++q)
+                if (tets[4 * j + q] < n_real) n2t[cur[tets[4 * j + q]]++] = (int)(4 * j + q);
     }
     int max_deg = 0, max_nbr = 0;
     // vertex -> vertex (neighbours through a shared tet)
@@ -293,7 +331,7 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
             int j = n2t[p] >> 2;
             for (int q = 0; q < 4; ++q) {
                 int v = tets[4 * (int64_t)j + q];
-                if (v != i) buf.push_back(v);
+                if (v != i && v < n_real) buf.push_back(v);
             }
         }
         std::sort(buf.begin(), buf.end());
@@ -305,6 +343,8 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     free_mesh_buffers(c);
     c->n_v = n_v;
     c->n_t = n_t;
+    c->n_e = n_real;
+    c->dim = dim;
     c->max_deg = max_deg;
     c->max_nbr = max_nbr;
     std::vector<float4> x4(n_v);
@@ -317,10 +357,10 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     CK(dalloc(&c->xyz, n_v));
     CK(dalloc(&c->tets, n_t));
     CK(dalloc(&c->n2t_ptr, n_v + 1));
-    CK(dalloc(&c->n2t, 4 * n_t));
+    CK(dalloc(&c->n2t, n_faces));
     CK(dalloc(&c->n2n_ptr, n_v + 1));
     CK(dalloc(&c->n2n, (int64_t)n2n.size()));
-    CK(dalloc(&c->frec, 4 * n_t));
+    CK(dalloc(&c->frec, n_faces));
     CK(dalloc(&c->pc, n_v));
     CK(dalloc(&c->fib, 3 * n_t));
     CK(dalloc(&c->cf, n_t));
@@ -341,16 +381,17 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     CK(dalloc(&c->adj_w, n_v));
     CK(dalloc(&c->proc, n_v));
     CK(dalloc(&c->dphi, n_v));
+    CK(cudaMemset(c->dphi, 0, sizeof(float) * n_v));
     CK(cudaMemcpy(c->xyz, x4.data(), sizeof(float4) * n_v, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->tets, tets, sizeof(int4) * n_t, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->n2t_ptr, n2t_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->n2t, n2t.data(), sizeof(int) * 4 * n_t, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2t, n2t.data(), sizeof(int) * n_faces, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->n2n_ptr, n2n_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->n2n, n2n.data(), sizeof(int) * n2n.size(), cudaMemcpyHostToDevice));
     {
         // face records in vertex->tet order: the three other vertices in slot order, code
-        std::vector<int4> fr(4 * n_t);
-        for (int64_t e = 0; e < 4 * n_t; ++e) {
+        std::vector<int4> fr(n_faces);
+        for (int64_t e = 0; e < n_faces; ++e) {
             const int code = n2t[e];
             const int64_t j = code >> 2;
             const int s = code & 3;
@@ -364,7 +405,7 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
 #undef CK
     if (err) {
         free_mesh_buffers(c);
-        c->n_v = c->n_t = 0;
+        c->n_v = c->n_t = c->n_e = 0;
         return from_cuda(err);
     }
     c->nb = 1;
@@ -373,12 +414,58 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     return GBP_OK;
 }
 
+gbp_status gbp_upload_mesh_2d(gbp_ctx *c, const float *xy, int64_t n_v, const int32_t *tris, int64_t n_t)
+{
+    if (!c || !xy || !tris || n_v < 3 || n_t < 1 || n_v + 1 >= (1ll << 30) || n_t >= (1ll << 29))
+        return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
+    for (int64_t i = 0; i < n_v; ++i)
+        for (int r = 0; r < 2; ++r) {
+            double v = xy[2 * i + r];
+            if (!std::isfinite(v)) return GBP_ERR_BAD_MESH;
+            lo[r] = std::min(lo[r], v);
+            hi[r] = std::max(hi[r], v);
+        }
+    const double ext = std::max(hi[0] - lo[0], hi[1] - lo[1]);
+    const double atol = 1e-12 * ext * ext;
+    for (int64_t j = 0; j < n_t; ++j) {
+        const int32_t *t = tris + 3 * j;
+        for (int q = 0; q < 3; ++q)
+            if (t[q] < 0 || t[q] >= n_v) return GBP_ERR_BAD_MESH;
+        if (t[0] == t[1] || t[0] == t[2] || t[1] == t[2]) return GBP_ERR_BAD_MESH;
+        const double ax = (double)xy[2 * t[1]] - xy[2 * t[0]], ay = (double)xy[2 * t[1] + 1] - xy[2 * t[0] + 1];
+        const double bx = (double)xy[2 * t[2]] - xy[2 * t[0]], by = (double)xy[2 * t[2] + 1] - xy[2 * t[0] + 1];
+        if (!(0.5 * (ax * by - ay * bx) > atol)) return GBP_ERR_BAD_MESH;  // counter-clockwise, not degenerate
+    }
+    // lift: (x, y, 0) and the apex above the centre of the bounding box; any
+    // height works (the apex is never reached), the extent keeps the tets well shaped
+    std::vector<float> xyz(3 * (n_v + 1));
+    for (int64_t i = 0; i < n_v; ++i) {
+        xyz[3 * i] = xy[2 * i];
+        xyz[3 * i + 1] = xy[2 * i + 1];
+        xyz[3 * i + 2] = 0.f;
+    }
+    xyz[3 * n_v] = (float)(0.5 * (lo[0] + hi[0]));
+    xyz[3 * n_v + 1] = (float)(0.5 * (lo[1] + hi[1]));
+    xyz[3 * n_v + 2] = (float)(ext > 0 ? ext : 1.0);
+    std::vector<int32_t> tets(4 * n_t);
+    for (int64_t j = 0; j < n_t; ++j) {
+        for (int q = 0; q < 3; ++q) tets[4 * j + q] = tris[3 * j + q];
+        tets[4 * j + 3] = (int32_t)n_v;
+    }
+    return build_mesh(c, xyz.data(), n_v + 1, tets.data(), n_t, n_v, 2);
+}
+
 gbp_status gbp_set_fibres(gbp_ctx *c, const float *fib)
 {
     if (!c || !fib) return GBP_ERR_INVALID_ARG;
     if (!c->n_t) return GBP_ERR_STATE;
     DeviceGuard g(c->device);
-    cudaError_t e = cudaMemcpyAsync(c->fib, fib, sizeof(float) * 3 * c->n_t, cudaMemcpyDeviceToDevice, c->stream);
+    cudaError_t e = c->dim == 2 ? restride(c, c->n_t, 2, fib, 3, c->fib)
+                                : cudaMemcpyAsync(c->fib, fib, sizeof(float) * 3 * c->n_t, cudaMemcpyDeviceToDevice,
+                                                  c->stream);
     if (e) return from_cuda(e);
     c->has_fib = true;
     c->has_vel = false;
@@ -415,11 +502,11 @@ gbp_status gbp_set_leadfield(gbp_ctx *c, const float *L, int32_t N)
     if (!c || !L || N < 1 || N > 16) return GBP_ERR_INVALID_ARG;
     if (!c->n_v) return GBP_ERR_STATE;
     DeviceGuard g(c->device);
-    cudaError_t e = dalloc(&c->L, (int64_t)N * c->n_v);
+    cudaError_t e = dalloc(&c->L, (int64_t)N * c->n_e);
     if (!e) e = dalloc(&c->Lrowsum, 16);
-    if (!e) e = cudaMemcpyAsync(c->L, L, sizeof(float) * N * c->n_v, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->L, L, sizeof(float) * N * c->n_e, cudaMemcpyDeviceToDevice, c->stream);
     if (!e) {
-        k_rowsum<<<N, 256, 0, c->stream>>>(c->n_v, c->L, c->Lrowsum);
+        k_rowsum<<<N, 256, 0, c->stream>>>(c->n_e, c->L, c->Lrowsum);
         c->launches++;
         e = cudaGetLastError();
     }
@@ -445,7 +532,9 @@ gbp_status gbp_set_onsets(gbp_ctx *c, int32_t kind, int32_t K, const int32_t *id
     }
     if (!e) e = cudaMemcpyAsync(c->on_idx, idx, sizeof(int) * K, cudaMemcpyDeviceToDevice, c->stream);
     if (!e && kind == GBP_ONSET_ELEMENT)
-        e = cudaMemcpyAsync(c->on_bary, bary, sizeof(float) * 4 * K, cudaMemcpyDeviceToDevice, c->stream);
+        e = c->dim == 2 ? restride(c, K, 3, bary, 4, c->on_bary)
+                        : cudaMemcpyAsync(c->on_bary, bary, sizeof(float) * 4 * K, cudaMemcpyDeviceToDevice,
+                                          c->stream);
     if (!e && kind == GBP_ONSET_NODAL) e = cudaMemsetAsync(c->on_bary, 0, sizeof(float) * 4 * K, c->stream);
     if (!e) e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * K, cudaMemcpyDeviceToDevice, c->stream);
     if (e) return from_cuda(e);
@@ -465,7 +554,8 @@ static gbp_solve_opts normalized_opts(const gbp_ctx *c, const gbp_solve_opts *o)
         r.eps = 0.f;
         r.max_iters = 0;
     }
-    if (r.max_iters <= 0) r.max_iters = (int)(8.0 * std::cbrt((double)c->n_v)) + 64 + r.n_f;
+    if (r.max_iters <= 0)
+        r.max_iters = (int)(8.0 * (c->dim == 2 ? std::sqrt((double)c->n_v) : std::cbrt((double)c->n_v))) + 64 + r.n_f;
     return r;
 }
 
@@ -537,12 +627,39 @@ gbp_status gbp_ecg_loss_backward(gbp_ctx *c, const float *phi, const float *ecg,
     return from_cuda(gbp::launch_ecg_backward(c, phi, ecg, target, tmpl, loss, dphi));
 }
 
+// The adjoint of the current solve (or batch of solves).  For a lifted
+// triangle mesh the caller's dLoss/dphi (n_e entries) is first copied into
+// the context's own array (the apex entries are never read: the apex is
+// unreached), and the onset-position gradient, computed as [..][3] with a
+// zero third component, is repacked to [..][2].
+static cudaError_t run_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_ct, float *d_t, float *d_x)
+{
+    if (c->dim != 2) return gbp::launch_adjoint(c, dphi, d_cf, d_ct, d_t, d_x);
+    cudaError_t e = cudaSuccess;
+    if (dphi != c->dphi) {
+        e = cudaMemcpyAsync(c->dphi, dphi, sizeof(float) * c->n_e, cudaMemcpyDeviceToDevice, c->stream);
+        dphi = c->dphi;
+    }
+    float *dx3 = nullptr;
+    if (!e && d_x) {
+        const int64_t need = 3 * (int64_t)c->K * c->nb;
+        if (need > c->dx3_cap) {
+            e = dalloc(&c->dx3, need);
+            c->dx3_cap = e ? 0 : need;
+        }
+        dx3 = c->dx3;
+    }
+    if (!e) e = gbp::launch_adjoint(c, dphi, d_cf, d_ct, d_t, dx3);
+    if (!e && d_x) e = restride(c, (int64_t)c->K * c->nb, 3, dx3, 2, d_x);
+    return e;
+}
+
 gbp_status gbp_geodesic_backward(gbp_ctx *c, const float *dphi, float *d_cf, float *d_ct, float *d_t, float *d_x)
 {
     if (!c || !dphi) return GBP_ERR_INVALID_ARG;
     if (c->solve_gen < 0 || c->solve_gen != c->param_gen) return GBP_ERR_STATE;
     DeviceGuard g(c->device);
-    return from_cuda(gbp::launch_adjoint(c, dphi, d_cf, d_ct, d_t, d_x));
+    return from_cuda(run_adjoint(c, dphi, d_cf, d_ct, d_t, d_x));
 }
 
 gbp_status gbp_forward_backward(gbp_ctx *c, const gbp_solve_opts *opts, const gbp_template *tmpl,
@@ -587,9 +704,9 @@ gbp_status gbp_forward_backward_host(gbp_ctx *c, const gbp_solve_opts *opts, con
     if (!c || !cf || !ct || !target || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
     if (!c->n_v || !c->has_fib || !c->K || !c->N) return GBP_ERR_STATE;
     DeviceGuard g(c->device);
-    const int64_t n_t = c->n_t, K = c->K, NT = (int64_t)c->N * tmpl->T;
+    const int64_t n_t = c->n_t, K = c->K, NT = (int64_t)c->N * tmpl->T, d = c->dim;
     // staging layout: in = [cf | ct | t | target], out = [loss | d_cf | d_ct | d_t | d_x]
-    const int64_t in_n = 2 * n_t + K + NT, out_n = 1 + 2 * n_t + 4 * K;
+    const int64_t in_n = 2 * n_t + K + NT, out_n = 1 + 2 * n_t + (1 + d) * K;
     cudaError_t e = cudaSuccess;
     if (in_n > c->stage_in_cap) {
         if (c->pin_in) cudaFreeHost(c->pin_in);
@@ -626,7 +743,7 @@ gbp_status gbp_forward_backward_host(gbp_ctx *c, const gbp_solve_opts *opts, con
     if (d_cf) std::memcpy(d_cf, po + 1, sizeof(float) * n_t);
     if (d_ct) std::memcpy(d_ct, po + 1 + n_t, sizeof(float) * n_t);
     if (d_t) std::memcpy(d_t, po + 1 + 2 * n_t, sizeof(float) * K);
-    if (d_x) std::memcpy(d_x, po + 1 + 2 * n_t + K, sizeof(float) * 3 * K);
+    if (d_x) std::memcpy(d_x, po + 1 + 2 * n_t + K, sizeof(float) * d * K);
     return GBP_OK;
 }
 
@@ -729,7 +846,7 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opt
             e = gbp::launch_ecg_backward(c, c->phi + b * n_v, V + b * NT, target + b * NT, tmpl, loss + b,
                                          c->dphi + b * n_v);
     }
-    if (!e) e = gbp::launch_adjoint(c, c->dphi, d_cf, d_ct, d_t, d_x);
+    if (!e) e = run_adjoint(c, c->dphi, d_cf, d_ct, d_t, d_x);
     // the context's single-problem state is gone: the next single-problem
     // evaluation starts from gbp_set_velocities
     c->nb = 1;

@@ -148,9 +148,9 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
     int T_tile, G;
     ecg_fwd_shape(T, &T_tile, &G);
     int ncta = 2 * c->num_sms;
-    int64_t per = (c->n_v + ncta - 1) / ncta;
+    int64_t per = (c->n_e + ncta - 1) / ncta;
     per = ((per + ECG_CH - 1) / ECG_CH) * ECG_CH;
-    ncta = (int)((c->n_v + per - 1) / per);
+    ncta = (int)((c->n_e + per - 1) / per);
     int64_t need = 2 * (int64_t)ncta * N * T;  // FP64 partials, counted in floats
     if (need > c->ecg_part_cap) {
         if (c->ecg_part) cudaFree(c->ecg_part);
@@ -166,7 +166,7 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
     size_t smem = ecg_fwd_smem(N, T_tile, G);
     float c4 = 4.f / t->tau;
     time_begin(c, 2);
-    cudaError_t le = launch_ecg_fwd_leads(N, ncta, T_tile * G, smem, c->stream, c->n_v, T, c->L, phi, t->t0, t->dt,
+    cudaError_t le = launch_ecg_fwd_leads(N, ncta, T_tile * G, smem, c->stream, c->n_e, T, c->L, phi, t->t0, t->dt,
                                           c4, T_tile, G, per, part);
     if (le) return le;
     k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, c->stream>>>(N, T, ncta, part, c->Lrowsum, t->K0, t->K1 - t->K0,
@@ -276,11 +276,11 @@ cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, 
     size_t smem = sizeof(float) * NT;  // N * T <= 16 * 4096 floats = 256 KB at most
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     float scale = -2.f / (float)NT * (t->K1 - t->K0) * (4.f / t->tau);
-    const unsigned blocks = (unsigned)((c->n_v + 255) / 256);
+    const unsigned blocks = (unsigned)((c->n_e + 255) / 256);
     cudaError_t le = cudaErrorInvalidValue;
     switch (N) {
 #define GBP_BWD_CASE(n) \
-    case n: le = launch_bwd_n<n>(blocks, smem, c->stream, c->n_v, T, c->L, phi, c->resid, t->t0, t->dt, t->tau, \
+    case n: le = launch_bwd_n<n>(blocks, smem, c->stream, c->n_e, T, c->L, phi, c->resid, t->t0, t->dt, t->tau, \
                                  scale, dphi); break;
         GBP_BWD_CASE(1) GBP_BWD_CASE(2) GBP_BWD_CASE(3) GBP_BWD_CASE(4) GBP_BWD_CASE(5) GBP_BWD_CASE(6)
         GBP_BWD_CASE(7) GBP_BWD_CASE(8) GBP_BWD_CASE(9) GBP_BWD_CASE(10) GBP_BWD_CASE(11) GBP_BWD_CASE(12)

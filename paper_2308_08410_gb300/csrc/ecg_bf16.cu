@@ -218,7 +218,7 @@ __global__ void k_lead_bf16(int64_t n_v, int64_t n_pad, int N, const float *__re
 
 cudaError_t prepare_leadfield_bf16(gbp_ctx *c)
 {
-    const int64_t n_pad = ((c->n_v + BF_KT - 1) / BF_KT) * BF_KT;
+    const int64_t n_pad = ((c->n_e + BF_KT - 1) / BF_KT) * BF_KT;
     cudaError_t e = cudaSuccess;
     if (c->Lbf) cudaFree(c->Lbf);
     c->Lbf = nullptr;
@@ -226,9 +226,9 @@ cudaError_t prepare_leadfield_bf16(gbp_ctx *c)
     if (!e && !c->Lscale) e = cudaMalloc(&c->Lscale, sizeof(float) * BF_N);
     if (e) return e;
     c->n_v_pad = n_pad;
-    k_lead_scale<<<c->N, 256, 0, c->stream>>>(c->n_v, c->L, c->Lscale);
+    k_lead_scale<<<c->N, 256, 0, c->stream>>>(c->n_e, c->L, c->Lscale);
     int64_t tot = (int64_t)BF_N * n_pad;
-    k_lead_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->n_v, n_pad, c->N, c->L, c->Lscale,
+    k_lead_bf16<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(c->n_e, n_pad, c->N, c->L, c->Lscale,
                                                                       c->Lbf);
     c->launches += 2;
     return cudaGetLastError();
@@ -252,9 +252,9 @@ cudaError_t launch_ecg_forward_bf16(gbp_ctx *c, const float *phi, const gbp_temp
     const int N = c->N, T = t->T;
     const int mtiles = (T + BF_M - 1) / BF_M;
     int nsplit = (4 * c->num_sms + mtiles - 1) / mtiles;
-    int64_t per = (c->n_v + nsplit - 1) / nsplit;
+    int64_t per = (c->n_e + nsplit - 1) / nsplit;
     per = ((per + BF_KT - 1) / BF_KT) * BF_KT;
-    nsplit = (int)((c->n_v + per - 1) / per);
+    nsplit = (int)((c->n_e + per - 1) / per);
     int64_t need = (int64_t)nsplit * BF_N * T;
     if (need > c->ecg_part_cap) {
         if (c->ecg_part) cudaFree(c->ecg_part);
@@ -267,7 +267,7 @@ cudaError_t launch_ecg_forward_bf16(gbp_ctx *c, const float *phi, const gbp_temp
         c->ecg_part_cap = need;
     }
     time_begin(c, 2);
-    k_ecg_bf16<<<dim3(nsplit, mtiles), 128, 0, c->stream>>>(c->n_v, c->n_v_pad, N, T, c->Lbf, phi, t->t0, t->dt,
+    k_ecg_bf16<<<dim3(nsplit, mtiles), 128, 0, c->stream>>>(c->n_e, c->n_v_pad, N, T, c->Lbf, phi, t->t0, t->dt,
                                                             4.f / t->tau, per, c->ecg_part, c->ctl);
     k_ecg_reduce_bf16<<<(N * T + 255) / 256, 256, 0, c->stream>>>(N, T, nsplit, c->ecg_part, c->Lrowsum, c->Lscale,
                                                                  t->K0, t->K1 - t->K0, ecg);

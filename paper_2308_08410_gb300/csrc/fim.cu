@@ -105,8 +105,10 @@ cudaError_t launch_lipschitz(gbp_ctx *c)
 // ---------------------------------------------------------------------------
 
 // Batched: thread g = b * K + k (onset times t [nb][K]; sites shared).
+// Vertices from n_real on (the apex of a lifted triangle mesh) take no key.
 __global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ idx, const float *__restrict__ bary,
-                             const float *__restrict__ t, int64_t n_v, int64_t n_t, const float4 *__restrict__ xyz,
+                             const float *__restrict__ t, int64_t n_v, int64_t n_real, int64_t n_t,
+                             const float4 *__restrict__ xyz,
                              const int4 *__restrict__ tets, const float4 *__restrict__ tm,
                              const float *__restrict__ tsd, unsigned long long *keys_all, Control *ctl)
 {
@@ -117,7 +119,7 @@ __global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ id
     const float tk = t[g];
     int id = idx[k];
     if (kind == GBP_ONSET_NODAL) {
-        if (id < 0 || id >= n_v) {
+        if (id < 0 || id >= n_real) {
             atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
             return;
         }
@@ -147,7 +149,7 @@ __global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ id
             float3 w = xform(make_float3(x[q].x - xo.x, x[q].y - xo.y, x[q].z - xo.z), m, sd);
             float v = tk + sqrtf(f3dot(w, w));
             unsigned long long key = ((unsigned long long)float_key(v) << 32) | (unsigned)k;
-            atomicMin(&keys[ids[q]], key);
+            if (ids[q] < n_real) atomicMin(&keys[ids[q]], key);
         }
     }
 }
@@ -485,7 +487,7 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     if (err) return err;
     int th = 256;
     k_onset_keys<<<(c->K * c->nb + th - 1) / th, th, 0, c->stream>>>(c->K, c->nb, c->onset_kind, c->on_idx,
-                                                                      c->on_bary, c->on_t, n_v, c->n_t, c->xyz,
+                                                                      c->on_bary, c->on_t, n_v, c->n_e, c->n_t, c->xyz,
                                                                       c->tets, c->tm, c->tsd, c->keys, c->ctl);
     unsigned bl = (unsigned)((n_tot + th - 1) / th);
     k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp, c->pc);
@@ -552,9 +554,12 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
 // ---------------------------------------------------------------------------
 // parent pass: alpha of the final parent face with the final values
 // ---------------------------------------------------------------------------
-// Batched: entry g = b * n_v + i.
+// Batched: entry g = b * n_v + i.  Outputs (single problem only) and the
+// unreached count cover the caller's vertices i < n_e; for a lifted triangle
+// mesh (dim 2) the code is written as triangle * 3 + slot and alpha as the
+// weights of the triangle's two other vertices (the apex weight is 0).
 template <int MODE>
-__global__ void k_parent_pass(int n_v, int n_tot, int64_t n_t, const float4 *__restrict__ xyz,
+__global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t, const float4 *__restrict__ xyz,
                               const int4 *__restrict__ tets, const float4 *__restrict__ tm_all,
                               const float *__restrict__ tsd_all, const float4 *__restrict__ tlip_all, int n_f,
                               const float *__restrict__ phi_all, int4 *rec, float *out_phi, int32_t *out_parent,
@@ -592,10 +597,18 @@ __global__ void k_parent_pass(int n_v, int n_tot, int64_t n_t, const float4 *__r
         a1 = lr.a1;
         a2 = lr.a2;
         rec[i] = make_int4(code, __float_as_int(a0), __float_as_int(a1), __float_as_int(a2));
-    } else if (code == GBP_UNREACHED) {
-        atomicAdd(&ctl->unreached, 1ull);
     }
+    if (i - b * n_v >= n_e) return;
+    if (code == GBP_UNREACHED) atomicAdd(&ctl->unreached, 1ull);
     if (out_phi) out_phi[i] = pv;
+    if (dim == 2) {
+        if (out_parent) out_parent[i] = code >= 0 ? (code >> 2) * 3 + (code & 3) : code;
+        if (out_alpha) {
+            out_alpha[2 * i] = a0;
+            out_alpha[2 * i + 1] = a1;
+        }
+        return;
+    }
     if (out_parent) out_parent[i] = code;
     if (out_alpha) {
         out_alpha[3 * i] = a0;
@@ -611,13 +624,13 @@ cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_
     unsigned bl = (unsigned)((n_tot + th - 1) / th);
     time_begin(c, 1);
     if (mode == GBP_LOCAL_FISTA)
-        k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>((int)c->n_v, n_tot, c->n_t, c->xyz, c->tets, c->tm,
-                                                                 c->tsd, c->tlip, n_f, c->phi, c->rec, phi, parent,
-                                                                 alpha, c->ctl);
+        k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
+                                                                 c->xyz, c->tets, c->tm, c->tsd, c->tlip, n_f,
+                                                                 c->phi, c->rec, phi, parent, alpha, c->ctl);
     else
-        k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>((int)c->n_v, n_tot, c->n_t, c->xyz, c->tets, c->tm,
-                                                                 c->tsd, c->tlip, n_f, c->phi, c->rec, phi, parent,
-                                                                 alpha, c->ctl);
+        k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
+                                                                 c->xyz, c->tets, c->tm, c->tsd, c->tlip, n_f,
+                                                                 c->phi, c->rec, phi, parent, alpha, c->ctl);
     time_end(c, 1);
     c->launches++;
     return cudaGetLastError();

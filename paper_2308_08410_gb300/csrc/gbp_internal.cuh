@@ -494,6 +494,17 @@ struct gbp_ctx {
     int num_sms = 0;
     int64_t n_v = 0, n_t = 0;
     int max_deg = 0;  // max vertex->tet degree
+    // Triangle meshes (d = 2) run lifted: triangle (a, b, c) becomes the tet
+    // (a, b, c, apex) with one apex above the plane shared by all of them,
+    // stored as the last vertex.  No vertex row lists the apex, no onset
+    // reaches it, so it stays at +inf and every face holding it reduces to
+    // the edge problem of the triangle (the local problem for d = 2).
+    // n_e = the caller's vertices (all but the apex): the ECG, the lead
+    // field and every per-vertex output cover those.
+    int dim = 3;
+    int64_t n_e = 0;
+    float *dx3 = nullptr;  // d = 2: [nb][K][3] onset-position gradient before the repack to [nb][K][2]
+    int64_t dx3_cap = 0;
     // Batch of independent problems on the same mesh (multi-start): every
     // per-problem array below holds nb_cap problems back to back ([b][n_v] or
     // [b][n_t]); the kernels of a call run nb of them.
@@ -515,7 +526,7 @@ struct gbp_ctx {
     float *on_bary = nullptr, *on_t = nullptr;
     // lead field
     int N = 0;
-    float *L = nullptr;            // [N][n_v]
+    float *L = nullptr;            // [N][n_e]
     __nv_bfloat16 *Lbf = nullptr;  // [16][n_v_pad] per-lead scaled
     float *Lscale = nullptr;       // [16]
     float *Lrowsum = nullptr;      // [16]

@@ -78,6 +78,7 @@ def load():
         "gbp_status_string": ([i32], C.c_char_p),
         "gbp_synchronize": ([P], i32),
         "gbp_upload_mesh": ([P, P, i64, P, i64], i32),
+        "gbp_upload_mesh_2d": ([P, P, i64, P, i64], i32),
         "gbp_set_fibres": ([P, P], i32),
         "gbp_set_velocities": ([P, P, P], i32),
         "gbp_set_leadfield": ([P, P, i32], i32),
@@ -125,7 +126,7 @@ def exported_symbols():
     """Names of the entry points this binding expects the library to export."""
     return [
         "gbp_create", "gbp_destroy", "gbp_set_stream", "gbp_status_string", "gbp_synchronize",
-        "gbp_upload_mesh", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
+        "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
         "gbp_set_onsets", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
         "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_local_solve_batch", "gbp_enable_timing",
@@ -186,6 +187,7 @@ class Context:
         _check(self.lib.gbp_create(C.byref(h), self.device, C.c_void_p(stream.cuda_stream)), "gbp_create")
         self.h = h
         self.n_v = self.n_t = self.N = self.K = 0
+        self.dim = 3
 
     def close(self):
         if getattr(self, "h", None):
@@ -209,6 +211,17 @@ class Context:
         _check(self.lib.gbp_upload_mesh(self.h, _hptr(xyz), xyz.shape[0], _hptr(tets), tets.shape[0]),
                "gbp_upload_mesh")
         self.n_v, self.n_t = xyz.shape[0], tets.shape[0]
+        self.dim = 3
+
+    def upload_mesh_2d(self, xy: np.ndarray, tris: np.ndarray):
+        """Triangle mesh (d = 2): xy [n_v, 2], tris [n_t, 3] counter-clockwise.
+        From here on fibres are [n_t, 2], alpha [n_v, 2], d_x [K, 2]."""
+        xy = np.ascontiguousarray(xy, np.float32)
+        tris = np.ascontiguousarray(tris, np.int32)
+        _check(self.lib.gbp_upload_mesh_2d(self.h, _hptr(xy), xy.shape[0], _hptr(tris), tris.shape[0]),
+               "gbp_upload_mesh_2d")
+        self.n_v, self.n_t = xy.shape[0], tris.shape[0]
+        self.dim = 2
 
     def set_fibres(self, fib):
         _check(self.lib.gbp_set_fibres(self.h, _ptr(fib)), "gbp_set_fibres")
@@ -231,7 +244,7 @@ class Context:
         dev = self.torch_device
         phi = torch.empty(self.n_v, dtype=torch.float32, device=dev) if phi is None else phi
         parent = torch.empty(self.n_v, dtype=torch.int32, device=dev) if parent is None else parent
-        alpha = torch.empty(self.n_v, 3, dtype=torch.float32, device=dev) if alpha is None else alpha
+        alpha = torch.empty(self.n_v, self.dim, dtype=torch.float32, device=dev) if alpha is None else alpha
         o = opts if opts is not None else make_opts()
         _check(self.lib.gbp_eikonal_solve(self.h, C.byref(o), _ptr(phi), _ptr(parent), _ptr(alpha)),
                "gbp_eikonal_solve")
@@ -270,7 +283,7 @@ class Context:
         d_cf = torch.empty(self.n_t, dtype=torch.float32, device=dev)
         d_ct = torch.empty(self.n_t, dtype=torch.float32, device=dev)
         d_t = torch.empty(self.K, dtype=torch.float32, device=dev)
-        d_x = torch.empty(self.K, 3, dtype=torch.float32, device=dev)
+        d_x = torch.empty(self.K, self.dim, dtype=torch.float32, device=dev)
         _check(self.lib.gbp_geodesic_backward(self.h, _ptr(dphi), _ptr(d_cf), _ptr(d_ct), _ptr(d_t),
                                               _ptr(d_x)), "gbp_geodesic_backward")
         return d_cf, d_ct, d_t, d_x
@@ -286,7 +299,7 @@ class Context:
                        d_cf=torch.empty(self.n_t, dtype=torch.float32, device=dev),
                        d_ct=torch.empty(self.n_t, dtype=torch.float32, device=dev),
                        d_t=torch.empty(self.K, dtype=torch.float32, device=dev),
-                       d_x=torch.empty(self.K, 3, dtype=torch.float32, device=dev))
+                       d_x=torch.empty(self.K, self.dim, dtype=torch.float32, device=dev))
         tm = make_template(tmpl)
         o = opts if opts is not None else make_opts()
         _check(self.lib.gbp_forward_backward(self.h, C.byref(o), C.byref(tm), int(precision), _ptr(cf),
@@ -305,7 +318,7 @@ class Context:
             f32 = dict(dtype=torch.float32, device=dev)
             out = dict(loss=torch.empty(B, **f32), ecg=torch.empty(B, self.N, tmpl.T, **f32),
                        d_cf=torch.empty(B, self.n_t, **f32), d_ct=torch.empty(B, self.n_t, **f32),
-                       d_t=torch.empty(B, self.K, **f32), d_x=torch.empty(B, self.K, 3, **f32))
+                       d_t=torch.empty(B, self.K, **f32), d_x=torch.empty(B, self.K, self.dim, **f32))
         tm = make_template(tmpl)
         o = opts if opts is not None else make_opts()
         _check(self.lib.gbp_forward_backward_batch(self.h, B, C.byref(o), C.byref(tm), int(precision), _ptr(cf),
@@ -321,7 +334,7 @@ class Context:
         if out is None:
             out = dict(loss=np.zeros(1, np.float32), d_cf=np.empty(self.n_t, np.float32),
                        d_ct=np.empty(self.n_t, np.float32), d_t=np.empty(self.K, np.float32),
-                       d_x=np.empty((self.K, 3), np.float32))
+                       d_x=np.empty((self.K, self.dim), np.float32))
         tm = make_template(tmpl)
         o = opts if opts is not None else make_opts()
         _check(self.lib.gbp_forward_backward_host(self.h, C.byref(o), C.byref(tm), int(precision),
@@ -401,6 +414,24 @@ def setup_problem(ctx: Context, problem) -> DeviceProblem:
     ctx.set_leadfield(L)
     ctx.set_onsets(ons.kind, idx, t, bary)
     return DeviceProblem(ctx, fib, cf, ct, L, idx, t, bary, ons.kind)
+
+
+def setup_problem_2d(ctx: Context, problem) -> DeviceProblem:
+    """Upload a seeded triangle-mesh problem (synth.Problem2D; nodal onsets)."""
+    import torch
+    dev = ctx.torch_device
+    ctx.upload_mesh_2d(problem.mesh.xy, problem.mesh.tris)
+
+    def up(a, dt=np.float32):
+        return torch.from_numpy(np.ascontiguousarray(a, dt)).to(dev)
+
+    fib, cf, ct, L = up(problem.fib), up(problem.cf), up(problem.ct), up(problem.L)
+    idx, t = up(problem.onset_nodes, np.int32), up(problem.onset_t)
+    ctx.set_fibres(fib)
+    ctx.set_velocities(cf, ct)
+    ctx.set_leadfield(L)
+    ctx.set_onsets(ONSET_NODAL, idx, t)
+    return DeviceProblem(ctx, fib, cf, ct, L, idx, t, None, ONSET_NODAL)
 
 
 def library_exists() -> bool:

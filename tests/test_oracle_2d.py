@@ -106,3 +106,61 @@ def test_adjoint_vs_finite_differences():
         e[k] = h
         fd = (loss(cf, ct, t + e)[0][0] - loss(cf, ct, t - e)[0][0]) / (2 * h)
         assert abs(fd - g["d_t"][k]) <= 1e-5 * max(abs(fd), 1e-8), (k, fd, g["d_t"][k])
+
+
+def test_element_onset_at_a_vertex_is_nodal():
+    p = S.make_2d(10, seed=2)
+    mesh = O2.Mesh2D(p.mesh.xy, p.mesh.tris)
+    E = 37
+    for q in range(3):
+        b = np.zeros((1, 3))
+        b[0, q] = 1.0
+        el = O2.eikonal(mesh, p.fib, p.cf, p.ct, [E], [2.0], b)
+        nod = O2.eikonal(mesh, p.fib, p.cf, p.ct, [mesh.tris[E][q]], [2.0])
+        np.testing.assert_allclose(el["phi"], nod["phi"], rtol=1e-13, atol=1e-13)
+
+
+def test_element_onset_gradients_vs_finite_differences():
+    p = S.make_2d(10, seed=6)
+    mesh = O2.Mesh2D(p.mesh.xy, p.mesh.tris)
+    cf, ct = p.cf.astype(np.float64), p.ct.astype(np.float64)
+    rng = np.random.default_rng(8)
+    tris = np.array([23, 101])
+    bary = rng.dirichlet(np.ones(3), size=2)
+    t = np.array([1.0, 4.0])
+
+    def run(t_, bary_, cf_=cf):
+        ek = O2.eikonal(mesh, p.fib, cf_, ct, tris, t_, bary_)
+        return ek, O.ecg(p.L, ek["phi"], p.tmpl)
+
+    target = S.add_noise(run(t + 0.5, bary)[1], 0.05, 9)
+
+    def loss(t_, bary_, cf_=cf):
+        ek, V = run(t_, bary_, cf_)
+        return O.loss_grad_phi(p.L, ek["phi"], p.tmpl, V, target)[0]
+
+    ek, V = run(t, bary)
+    _, lam = O.loss_grad_phi(p.L, ek["phi"], p.tmpl, V, target)
+    g = O2.adjoint(mesh, p.fib, cf, ct, tris, ek["parent"], ek["alpha"], lam, t, bary)
+    h = 1e-6
+    for k in range(2):
+        e = np.zeros(2)
+        e[k] = h
+        fd = (loss(t + e, bary) - loss(t - e, bary)) / (2 * h)
+        assert abs(fd - g["d_t"][k]) <= 1e-5 * max(abs(fd), 1e-8), (k, fd, g["d_t"][k])
+        # moving x_k along a direction u inside the triangle: d bary = M^{-1} [u; 0]
+        V3 = mesh.xy[mesh.tris[tris[k]]]
+        Minv = np.linalg.inv(np.vstack([V3.T, np.ones(3)]))
+        for u in (np.array([1.0, 0.0]), np.array([0.0, 1.0])):
+            db = Minv @ np.append(u, 0.0)
+            bp, bm = bary.copy(), bary.copy()
+            bp[k] += h * db
+            bm[k] -= h * db
+            fd = (loss(t, bp) - loss(t, bm)) / (2 * h)
+            assert abs(fd - g["d_x"][k] @ u) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g["d_x"]).max()), (k, u, fd)
+    # the onset triangle's velocity enters through the onset values too
+    for E in tris:
+        e = np.zeros_like(cf)
+        e[E] = h
+        fd = (loss(t, bary, cf + e) - loss(t, bary, cf - e)) / (2 * h)
+        assert abs(fd - g["d_cf"][E]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g["d_cf"]).max()), (E, fd, g["d_cf"][E])
