@@ -168,6 +168,20 @@ gbp_status gbp_set_leadfield(gbp_ctx *ctx, const float *L, int32_t N);
 gbp_status gbp_set_onsets(gbp_ctx *ctx, int32_t kind, int32_t K, const int32_t *idx,
                           const float *bary, const float *t);
 
+/* One set of onset sites per problem for gbp_forward_backward_batch with
+ * the same B (multi-start over the sites themselves, Sec. IV: the paper
+ * names batched optimisation as the way out of local minima of the site
+ * fit).  Layouts as gbp_set_onsets with a leading B: idx int32 [B][K],
+ * bary float32 [B][K][d + 1] (element onsets), t float32 [B][K] (the times
+ * the batched call uses when its own t is NULL).  Device pointers, copied.
+ * Grows the per-problem arrays to B problems like the batched call.  Until
+ * the next gbp_set_onsets, a batched call with another B is GBP_ERR_STATE,
+ * and single-problem calls use problem 0's sites.  Errors:
+ * GBP_ERR_INVALID_ARG, GBP_ERR_STATE (no mesh), GBP_ERR_NO_MEMORY; ids out
+ * of range are latched as in gbp_set_onsets. */
+gbp_status gbp_set_onsets_batch(gbp_ctx *ctx, int32_t kind, int32_t B, int32_t K, const int32_t *idx,
+                                const float *bary, const float *t);
+
 /* ------------------------------------------------------------------ */
 /* the hot path                                                         */
 /* ------------------------------------------------------------------ */
@@ -235,16 +249,19 @@ gbp_status gbp_forward_backward_host(gbp_ctx *ctx, const gbp_solve_opts *opts,
                                      const float *target, float *loss, float *d_cf,
                                      float *d_ct, float *d_t, float *d_x);
 
-/* B independent evaluations on the same mesh, fibres, lead field and onset
- * sites in one pass (multi-start: the paper suggests several starts against
- * local minima of the inverse problem, Sec. IV).  Each problem b has its own
- * velocities, onset times and target; the FIM, the parent pass and the
+/* B independent evaluations on the same mesh, fibres and lead field in one
+ * pass (multi-start: the paper suggests several starts against local minima
+ * of the inverse problem, Sec. IV).  The onset sites are those of
+ * gbp_set_onsets, shared by all problems, or one set per problem after
+ * gbp_set_onsets_batch.  Each problem b has its own velocities, onset times
+ * and target; the FIM, the parent pass and the
  * adjoint run all B problems in the same launches, so their per-iteration
  * latency is shared.  cf, ct device float32 [B][n_t]; t device float32
- * [B][K] (NULL: every problem uses the times of gbp_set_onsets); target
- * device float32 [B][N][T]; outputs device: loss [B], ecg [B][N][T] (may be
- * NULL), d_cf, d_ct [B][n_t], d_t [B][K], d_x [B][K][3] (any may be NULL).
- * Requires B * n_v < 2^31 / 3 and N * T <= 51200.  Grows the context's
+ * [B][K] (NULL: the times of gbp_set_onsets for every problem, or those of
+ * gbp_set_onsets_batch); target device float32 [B][N][T]; outputs device:
+ * loss [B], ecg [B][N][T] (may be NULL), d_cf, d_ct [B][n_t], d_t [B][K],
+ * d_x [B][K][d] (any may be NULL).  Requires B * n_v < 2^31 / 3 and
+ * N * T <= 51200; after gbp_set_onsets_batch, B equal to its B.  Grows the context's
  * per-problem arrays to B problems on first use (allocation, synchronises
  * once).  Afterwards the single-problem state is reset: the next
  * single-problem solve needs gbp_set_velocities first.  Statistics

@@ -48,6 +48,7 @@ struct AdjArgs {
     const float *cf, *ct;
     const int4 *rec;
     int onset_kind;
+    int site_per_problem;  // on_idx / on_bary hold one site set per problem
     const int *on_idx;
     const float *on_bary;
     const float *lam;
@@ -104,7 +105,8 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, 
         const int bk = b * a.K + k;
         if (a.d_t) atomicAdd(&a.d_t[bk], m);
         if (a.onset_kind == GBP_ONSET_ELEMENT) {
-            const int E = __ldg(&a.on_idx[k]);
+            const int sk = a.site_per_problem ? bk : k;
+            const int E = __ldg(&a.on_idx[sk]);
             const int4 tv = __ldg(&a.tets[E]);
             int ids[4] = {tv.x, tv.y, tv.z, tv.w};
             const float4 xi = __ldg(&a.xyz[i]);
@@ -112,7 +114,7 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, 
             float3 w = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                float b = __ldg(&a.on_bary[4 * k + q]);
+                float b = __ldg(&a.on_bary[4 * sk + q]);
                 float4 xq = __ldg(&a.xyz[ids[q]]);
                 w.x = fmaf(b, xi.x - xq.x, w.x);
                 w.y = fmaf(b, xi.y - xq.y, w.y);
@@ -571,6 +573,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.ct = c->ct;
     a.rec = c->rec;
     a.onset_kind = c->onset_kind;
+    a.site_per_problem = c->site_b > 0;
     a.on_idx = c->on_idx;
     a.on_bary = c->on_bary;
     a.lam = dphi;

@@ -85,6 +85,8 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->on_idx);
     dfree(&c->on_bary);
     dfree(&c->on_t);
+    c->site_cap = 0;
+    c->site_b = 0;
     dfree(&c->dphi);
     dfree(&c->dx3);
     c->dx3_cap = 0;
@@ -261,6 +263,7 @@ gbp_status gbp_synchronize(gbp_ctx *c)
 
 static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t,
                              int64_t n_real, int dim);
+static cudaError_t ensure_batch(gbp_ctx *c, int B);
 
 gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
 {
@@ -516,6 +519,30 @@ gbp_status gbp_set_leadfield(gbp_ctx *c, const float *L, int32_t N)
     return from_cuda(e);
 }
 
+// Copy n site entries (ids, barycentric coordinates in the caller's layout,
+// times) into the context's onset arrays, growing them first.  on_t keeps
+// room for K times per problem of the batch capacity.
+static cudaError_t store_sites(gbp_ctx *c, int32_t kind, int32_t K, int64_t n, const int32_t *idx, const float *bary,
+                               const float *t)
+{
+    cudaError_t e = cudaSuccess;
+    if (n > c->site_cap) {
+        e = dalloc(&c->on_idx, n);
+        if (!e) e = dalloc(&c->on_bary, 4 * n);
+        c->site_cap = e ? 0 : n;
+    }
+    const int64_t nt = std::max<int64_t>(n, (int64_t)K * c->nb_cap);
+    if (!e && (K != c->K || n > (int64_t)K * c->nb_cap)) e = dalloc(&c->on_t, nt);
+    if (!e) e = cudaMemcpyAsync(c->on_idx, idx, sizeof(int) * n, cudaMemcpyDeviceToDevice, c->stream);
+    if (!e && kind == GBP_ONSET_ELEMENT)
+        e = c->dim == 2 ? restride(c, n, 3, bary, 4, c->on_bary)
+                        : cudaMemcpyAsync(c->on_bary, bary, sizeof(float) * 4 * n, cudaMemcpyDeviceToDevice,
+                                          c->stream);
+    if (!e && kind == GBP_ONSET_NODAL) e = cudaMemsetAsync(c->on_bary, 0, sizeof(float) * 4 * n, c->stream);
+    if (!e) e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * n, cudaMemcpyDeviceToDevice, c->stream);
+    return e;
+}
+
 gbp_status gbp_set_onsets(gbp_ctx *c, int32_t kind, int32_t K, const int32_t *idx, const float *bary,
                           const float *t)
 {
@@ -524,22 +551,30 @@ gbp_status gbp_set_onsets(gbp_ctx *c, int32_t kind, int32_t K, const int32_t *id
     if (kind == GBP_ONSET_ELEMENT && !bary) return GBP_ERR_INVALID_ARG;
     if (!c->n_v) return GBP_ERR_STATE;
     DeviceGuard g(c->device);
-    cudaError_t e = cudaSuccess;
-    if (K != c->K) {
-        e = dalloc(&c->on_idx, K);
-        if (!e) e = dalloc(&c->on_bary, 4 * K);
-        if (!e) e = dalloc(&c->on_t, (int64_t)K * c->nb_cap);
-    }
-    if (!e) e = cudaMemcpyAsync(c->on_idx, idx, sizeof(int) * K, cudaMemcpyDeviceToDevice, c->stream);
-    if (!e && kind == GBP_ONSET_ELEMENT)
-        e = c->dim == 2 ? restride(c, K, 3, bary, 4, c->on_bary)
-                        : cudaMemcpyAsync(c->on_bary, bary, sizeof(float) * 4 * K, cudaMemcpyDeviceToDevice,
-                                          c->stream);
-    if (!e && kind == GBP_ONSET_NODAL) e = cudaMemsetAsync(c->on_bary, 0, sizeof(float) * 4 * K, c->stream);
-    if (!e) e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * K, cudaMemcpyDeviceToDevice, c->stream);
+    cudaError_t e = store_sites(c, kind, K, K, idx, bary, t);
     if (e) return from_cuda(e);
     c->K = K;
     c->onset_kind = kind;
+    c->site_b = 0;
+    c->param_gen++;
+    return GBP_OK;
+}
+
+gbp_status gbp_set_onsets_batch(gbp_ctx *c, int32_t kind, int32_t B, int32_t K, const int32_t *idx,
+                                const float *bary, const float *t)
+{
+    if (!c || !idx || !t || B < 1 || K < 1 || K > 65536) return GBP_ERR_INVALID_ARG;
+    if (kind != GBP_ONSET_NODAL && kind != GBP_ONSET_ELEMENT) return GBP_ERR_INVALID_ARG;
+    if (kind == GBP_ONSET_ELEMENT && !bary) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v || c->nb_cap < 1) return GBP_ERR_STATE;
+    if ((int64_t)B * c->n_v >= (1ll << 31) / 3 || (int64_t)B * K >= (1ll << 31) / 4) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaError_t e = ensure_batch(c, B);
+    if (!e) e = store_sites(c, kind, K, (int64_t)B * K, idx, bary, t);
+    if (e) return from_cuda(e);
+    c->K = K;
+    c->onset_kind = kind;
+    c->site_b = B;
     c->param_gen++;
     return GBP_OK;
 }
@@ -747,7 +782,8 @@ gbp_status gbp_forward_backward_host(gbp_ctx *c, const gbp_solve_opts *opts, con
     return GBP_OK;
 }
 
-// Grow the per-problem arrays to hold B problems (contents are not kept).
+// Grow the per-problem arrays to hold B problems (contents are not kept,
+// except the first K onset times).
 static cudaError_t ensure_batch(gbp_ctx *c, int B)
 {
     if (B <= c->nb_cap) return cudaSuccess;
@@ -777,7 +813,18 @@ static cudaError_t ensure_batch(gbp_ctx *c, int B)
     CK(dalloc(&c->proc, nv));
     CK(dalloc(&c->dphi, nv));
     CK(dalloc(&c->pc, nv));
-    if (c->K) CK(dalloc(&c->on_t, (int64_t)c->K * B));
+    if (c->K && !err) {
+        // grow the onset times keeping problem 0's (the shared times of gbp_set_onsets)
+        float *nt_ = nullptr;
+        CK(dalloc(&nt_, (int64_t)c->K * B));
+        CK(cudaMemcpy(nt_, c->on_t, sizeof(float) * c->K, cudaMemcpyDeviceToDevice));
+        if (!err) {
+            dfree(&c->on_t);
+            c->on_t = nt_;
+        } else {
+            dfree(&nt_);
+        }
+    }
 #undef CK
     c->has_vel = false;
     c->lip_valid = false;
@@ -799,6 +846,7 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opt
     if (!c || B < 1 || !cf || !ct || !target || !loss || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
     if (precision != GBP_PREC_FP32 && precision != GBP_PREC_BF16) return GBP_ERR_INVALID_ARG;
     if (!c->n_v || !c->has_fib || !c->K || !c->N || c->nb_cap < 1) return GBP_ERR_STATE;
+    if (c->site_b > 0 && B != c->site_b) return GBP_ERR_STATE;  // per-problem sites are for B problems
     if ((int64_t)B * c->n_v >= (1ll << 31) / 3 || (int64_t)B * c->n_t >= (1ll << 31)) return GBP_ERR_INVALID_ARG;
     if ((int64_t)c->N * tmpl->T > 51200) return GBP_ERR_INVALID_ARG;
     gbp_solve_opts o = normalized_opts(c, opts);
@@ -823,7 +871,7 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opt
     if (!e) e = cudaMemcpyAsync(c->ct, ct, sizeof(float) * n_t * B, cudaMemcpyDeviceToDevice, c->stream);
     if (t) {
         if (!e) e = cudaMemcpyAsync(c->on_t, t, sizeof(float) * K * B, cudaMemcpyDeviceToDevice, c->stream);
-    } else {
+    } else if (c->site_b == 0) {
         for (int b = 1; b < B && !e; ++b)
             e = cudaMemcpyAsync(c->on_t + b * K, c->on_t, sizeof(float) * K, cudaMemcpyDeviceToDevice, c->stream);
     }

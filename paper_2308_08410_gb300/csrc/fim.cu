@@ -104,9 +104,11 @@ cudaError_t launch_lipschitz(gbp_ctx *c)
 // onset seeding (Algorithm 2 initialisation, Eq. upwind_xi)
 // ---------------------------------------------------------------------------
 
-// Batched: thread g = b * K + k (onset times t [nb][K]; sites shared).
+// Batched: thread g = b * K + k (onset times t [nb][K]; sites shared, or
+// one set per problem when per_problem is set: idx [nb][K], bary [nb][K][4]).
 // Vertices from n_real on (the apex of a lifted triangle mesh) take no key.
-__global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ idx, const float *__restrict__ bary,
+__global__ void k_onset_keys(int K, int nb, int per_problem, int kind, const int *__restrict__ idx,
+                             const float *__restrict__ bary,
                              const float *__restrict__ t, int64_t n_v, int64_t n_real, int64_t n_t,
                              const float4 *__restrict__ xyz,
                              const int4 *__restrict__ tets, const float4 *__restrict__ tm,
@@ -117,7 +119,8 @@ __global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ id
     const int b = g / K, k = g - b * K;
     unsigned long long *keys = keys_all + (int64_t)b * n_v;
     const float tk = t[g];
-    int id = idx[k];
+    const int sk = per_problem ? g : k;
+    int id = idx[sk];
     if (kind == GBP_ONSET_NODAL) {
         if (id < 0 || id >= n_real) {
             atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
@@ -137,7 +140,7 @@ __global__ void k_onset_keys(int K, int nb, int kind, const int *__restrict__ id
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             x[q] = xyz[ids[q]];
-            float b = bary[4 * k + q];
+            float b = bary[4 * sk + q];
             xo.x = fmaf(b, x[q].x, xo.x);
             xo.y = fmaf(b, x[q].y, xo.y);
             xo.z = fmaf(b, x[q].z, xo.z);
@@ -486,7 +489,8 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     err = cudaMemsetAsync(c->keys, 0xff, sizeof(unsigned long long) * n_tot, c->stream);
     if (err) return err;
     int th = 256;
-    k_onset_keys<<<(c->K * c->nb + th - 1) / th, th, 0, c->stream>>>(c->K, c->nb, c->onset_kind, c->on_idx,
+    k_onset_keys<<<(c->K * c->nb + th - 1) / th, th, 0, c->stream>>>(c->K, c->nb, c->site_b > 0,
+                                                                      c->onset_kind, c->on_idx,
                                                                       c->on_bary, c->on_t, n_v, c->n_e, c->n_t, c->xyz,
                                                                       c->tets, c->tm, c->tsd, c->keys, c->ctl);
     unsigned bl = (unsigned)((n_tot + th - 1) / th);

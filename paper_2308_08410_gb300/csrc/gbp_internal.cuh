@@ -524,6 +524,10 @@ struct gbp_ctx {
     int onset_kind = 0, K = 0;
     int *on_idx = nullptr;
     float *on_bary = nullptr, *on_t = nullptr;
+    // sites of the batched call: 0 = one set shared by all problems
+    // (on_idx [K], on_bary [K][4]); B = one set per problem ([B][K], [B][K][4])
+    int site_b = 0;
+    int64_t site_cap = 0;  // site entries allocated in on_idx / on_bary
     // lead field
     int N = 0;
     float *L = nullptr;            // [N][n_e]

@@ -83,6 +83,7 @@ def load():
         "gbp_set_velocities": ([P, P, P], i32),
         "gbp_set_leadfield": ([P, P, i32], i32),
         "gbp_set_onsets": ([P, i32, i32, P, P, P], i32),
+        "gbp_set_onsets_batch": ([P, i32, i32, i32, P, P, P], i32),
         "gbp_eikonal_solve": ([P, C.POINTER(SolveOpts), P, P, P], i32),
         "gbp_get_solve_stats": ([P, C.POINTER(SolveStats)], i32),
         "gbp_ecg_forward": ([P, P, C.POINTER(Template), i32, P], i32),
@@ -127,7 +128,7 @@ def exported_symbols():
     return [
         "gbp_create", "gbp_destroy", "gbp_set_stream", "gbp_status_string", "gbp_synchronize",
         "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
-        "gbp_set_onsets", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
+        "gbp_set_onsets", "gbp_set_onsets_batch", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
         "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_local_solve_batch", "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
@@ -237,6 +238,14 @@ class Context:
         _check(self.lib.gbp_set_onsets(self.h, int(kind), idx.shape[0], _ptr(idx), _ptr(bary), _ptr(t)),
                "gbp_set_onsets")
         self.K = idx.shape[0]
+
+    def set_onsets_batch(self, kind, idx, t, bary=None):
+        """One site set per problem of the next batched calls: idx [B, K],
+        t [B, K], bary [B, K, d + 1] (element onsets)."""
+        B, K = int(idx.shape[0]), int(idx.shape[1])
+        _check(self.lib.gbp_set_onsets_batch(self.h, int(kind), B, K, _ptr(idx), _ptr(bary), _ptr(t)),
+               "gbp_set_onsets_batch")
+        self.K = K
 
     # ---- hot path -----------------------------------------------------------
     def eikonal_solve(self, opts: SolveOpts | None = None, phi=None, parent=None, alpha=None):
@@ -417,7 +426,8 @@ def setup_problem(ctx: Context, problem) -> DeviceProblem:
 
 
 def setup_problem_2d(ctx: Context, problem) -> DeviceProblem:
-    """Upload a seeded triangle-mesh problem (synth.Problem2D; nodal onsets)."""
+    """Upload a seeded triangle-mesh problem (synth.Problem2D): its element
+    onsets when it has them (problem.onsets), else its nodal ones."""
     import torch
     dev = ctx.torch_device
     ctx.upload_mesh_2d(problem.mesh.xy, problem.mesh.tris)
@@ -426,12 +436,17 @@ def setup_problem_2d(ctx: Context, problem) -> DeviceProblem:
         return torch.from_numpy(np.ascontiguousarray(a, dt)).to(dev)
 
     fib, cf, ct, L = up(problem.fib), up(problem.cf), up(problem.ct), up(problem.L)
-    idx, t = up(problem.onset_nodes, np.int32), up(problem.onset_t)
+    ons = getattr(problem, "onsets", None)
+    if ons is None:
+        kind, idx, t, bary = ONSET_NODAL, up(problem.onset_nodes, np.int32), up(problem.onset_t), None
+    else:
+        kind, idx, t = ons.kind, up(ons.idx, np.int32), up(ons.t)
+        bary = up(ons.bary) if ons.bary is not None else None
     ctx.set_fibres(fib)
     ctx.set_velocities(cf, ct)
     ctx.set_leadfield(L)
-    ctx.set_onsets(ONSET_NODAL, idx, t)
-    return DeviceProblem(ctx, fib, cf, ct, L, idx, t, None, ONSET_NODAL)
+    ctx.set_onsets(kind, idx, t, bary)
+    return DeviceProblem(ctx, fib, cf, ct, L, idx, t, bary, kind)
 
 
 def library_exists() -> bool:

@@ -8,7 +8,8 @@ recomputed on every call; no per-iteration solver state is stored, unlike
 backpropagation through the unrolled iterations of Algorithm 2).
 
 ``InverseProblem`` holds the parameter maps (per-vertex log velocities ->
-per-tet velocities, onset positions inside their tets) and runs Adam
+per-element velocities, onset positions inside their elements; tets, or
+triangles for the d = 2 study of Sec. III-A) and runs Adam
 (Sec. II-D: "gradient-based optimization utilizing ADAM").  The maps and the
 optimiser are ordinary torch operations; every step of the hot path runs in
 the library's kernels.
@@ -45,51 +46,59 @@ class InverseProblem:
     for a seeded problem uploaded to a context."""
 
     def __init__(self, ctx: gbp.Context, problem, target: np.ndarray, opts=None, precision=gbp.PREC_FP32,
-                 init_log_cf=None, init_log_ct=None, init_t=None, optimise_positions=True, relocate=True):
+                 init_log_cf=None, init_log_ct=None, init_t=None, optimise_positions=True, relocate=True,
+                 optimise_velocities=True):
         self.ctx = ctx
         self.p = problem
         dev = ctx.torch_device
-        self.dp = gbp.setup_problem(ctx, problem)
-        self.tets = torch.from_numpy(problem.mesh.tets.astype(np.int64)).to(dev)
+        # triangle meshes (d = 2) carry xy / tris, tet meshes xyz / tets
+        self.dim = 2 if hasattr(problem.mesh, "tris") else 3
+        X = problem.mesh.xy if self.dim == 2 else problem.mesh.xyz
+        cells = problem.mesh.tris if self.dim == 2 else problem.mesh.tets
+        self.X = np.asarray(X, np.float64)
+        self.dp = gbp.setup_problem_2d(ctx, problem) if self.dim == 2 else gbp.setup_problem(ctx, problem)
+        self.tets = torch.from_numpy(cells.astype(np.int64)).to(dev)
+        self.optimise_velocities = optimise_velocities
         n_v = problem.mesh.n_v
+        w = self.dim + 1
         lcf = np.full(n_v, np.log(0.6)) if init_log_cf is None else init_log_cf
         lct = np.full(n_v, np.log(0.3)) if init_log_ct is None else init_log_ct
-        t0 = problem.onsets.t if init_t is None else init_t
-        self.log_cf = torch.tensor(np.asarray(lcf, np.float32), device=dev, requires_grad=True)
-        self.log_ct = torch.tensor(np.asarray(lct, np.float32), device=dev, requires_grad=True)
-        self.t = torch.tensor(np.asarray(t0, np.float32), device=dev, requires_grad=True)
         ons = problem.onsets
+        t0 = ons.t if init_t is None else init_t
+        self.log_cf = torch.tensor(np.asarray(lcf, np.float32), device=dev, requires_grad=optimise_velocities)
+        self.log_ct = torch.tensor(np.asarray(lct, np.float32), device=dev, requires_grad=optimise_velocities)
+        self.t = torch.tensor(np.asarray(t0, np.float32), device=dev, requires_grad=True)
         self.kind = ons.kind
         self.optimise_positions = optimise_positions and ons.kind == gbp.ONSET_ELEMENT
         if ons.kind == gbp.ONSET_ELEMENT:
-            V = problem.mesh.xyz.astype(np.float64)[problem.mesh.tets[ons.idx]]  # [K, 4, 3]
+            V = self.X[cells[ons.idx]]  # [K, d + 1, d]
             x0 = np.einsum("kq,kqr->kr", ons.bary.astype(np.float64), V)
-            M = np.concatenate([V.transpose(0, 2, 1), np.ones((ons.K, 1, 4))], axis=1)  # [K, 4, 4]
+            M = np.concatenate([V.transpose(0, 2, 1), np.ones((ons.K, 1, w))], axis=1)  # [K, d + 1, d + 1]
             self.Vt_inv = torch.tensor(np.linalg.inv(M), dtype=torch.float32, device=dev)
             self.x = torch.tensor(x0.astype(np.float32), device=dev, requires_grad=self.optimise_positions)
         else:
             self.Vt_inv = None
-            self.x = torch.zeros(ons.K, 3, device=dev)
+            self.x = torch.zeros(ons.K, self.dim, device=dev)
         self.locator = None
         if self.optimise_positions and relocate:
-            from .relocate import TetLocator
-            self.locator = TetLocator(problem.mesh.xyz, problem.mesh.tets)
+            from .relocate import SimplexLocator
+            self.locator = SimplexLocator(self.X, cells)
         self.op = EvalOp(ctx=ctx, kind=ons.kind, on_idx=self.dp.on_idx,
                          target=torch.from_numpy(np.ascontiguousarray(target, np.float32)).to(dev),
                          tmpl=problem.tmpl, opts=opts if opts is not None else gbp.make_opts(),
                          precision=precision, phi=torch.empty(n_v, device=dev),
                          parent=torch.empty(n_v, dtype=torch.int32, device=dev),
-                         alpha=torch.empty(n_v, 3, device=dev),
+                         alpha=torch.empty(n_v, self.dim, device=dev),
                          ecg=torch.empty(problem.L.shape[0], problem.tmpl.T, device=dev))
 
     def params(self):
-        ps = [self.log_cf, self.log_ct, self.t]
+        ps = [self.log_cf, self.log_ct, self.t] if self.optimise_velocities else [self.t]
         if self.optimise_positions:
             ps.append(self.x)
         return ps
 
     def tet_velocities(self):
-        """Per-tet velocity = exp(mean of the four vertex log values)."""
+        """Per-element velocity = exp(mean of the element's vertex log values)."""
         return VertexLogToTet.apply(self.log_cf, self.tets), VertexLogToTet.apply(self.log_ct, self.tets)
 
     def bary(self):
@@ -116,7 +125,7 @@ class InverseProblem:
             return
         b = self.bary().clamp_min(floor)
         b = b / b.sum(dim=1, keepdim=True)
-        V = torch.from_numpy(self.p.mesh.xyz.astype(np.float32)).to(self.x.device)[self.tets[self.op.on_idx.long()]]
+        V = torch.from_numpy(self.X.astype(np.float32)).to(self.x.device)[self.tets[self.op.on_idx.long()]]
         self.x.copy_(torch.einsum("kq,kqr->kr", b, V))
 
     def run_adam(self, iters=500, lr=1e-2, log_every=0, callback=None):
@@ -138,10 +147,11 @@ class InverseProblem:
 
 
 class VertexLogToTet(torch.autograd.Function):
-    """c_j = exp(mean of the four vertex values of log c over tet j).  The
-    backward scatters g_j c_j / 4 to the tet's vertices with an atomic
-    index_add (autograd's own backward of the gather sorts the indices,
-    which dominates an inverse-loop step at 2M tets)."""
+    """c_j = exp(mean of the w vertex values of log c over element j (w = 4
+    for tets, 3 for triangles)).  The backward scatters g_j c_j / w to the
+    element's vertices with an atomic index_add (autograd's own backward of
+    the gather sorts the indices, which dominates an inverse-loop step at 2M
+    tets)."""
 
     @staticmethod
     def forward(fctx, logc, tets):
@@ -153,7 +163,8 @@ class VertexLogToTet(torch.autograd.Function):
     @staticmethod
     def backward(fctx, g):
         c, tets = fctx.saved_tensors
-        w = (0.25 * g * c).unsqueeze(1).expand(-1, 4).reshape(-1)
+        nw = tets.shape[1]
+        w = (g * c / nw).unsqueeze(1).expand(-1, nw).reshape(-1)
         out = torch.zeros(fctx.n, dtype=g.dtype, device=g.device)
         out.index_add_(0, tets.reshape(-1), w)
         return out, None
@@ -162,7 +173,7 @@ class VertexLogToTet(torch.autograd.Function):
 class GeodesicEcgLoss(torch.autograd.Function):
     """loss = 1/(N T) sum (ECG(phi(cf, ct, t, x)) - target)^2 (Eq. inverse_ecg).
 
-    Inputs: cf, ct per tet [n_t]; t onset times [K]; x onset positions [K, 3]
+    Inputs: cf, ct per element [n_t]; t onset times [K]; x onset positions [K, d]
     (element onsets; zeros for nodal ones), bary the barycentric coordinates
     of x in the onset tets (what the library consumes; derived from x outside
     the graph).  Forward: eikonal solve + ECG + misfit; backward: the
@@ -249,17 +260,192 @@ def run_c3(iters: int = 500, lr: float = 1e-2, n: int = 72, device: int = 0, log
     return res
 
 
+class MultiStartInverse:
+    """B starts of the site fit run together (Sec. IV: batched optimisation
+    as the way out of local minima).  Adam on every start's element-onset
+    positions and times ([B, K, d], [B, K]) with the velocities fixed; each
+    epoch is one batched evaluation (gbp_set_onsets_batch, then
+    gbp_forward_backward_batch: the FIM, parent pass and adjoint of all
+    starts share their launches).  The starts stay independent: each loss
+    depends on its own start only and Adam acts elementwise."""
+
+    def __init__(self, ctx: gbp.Context, problem, target: np.ndarray, starts, opts=None, precision=gbp.PREC_FP32,
+                 relocate=True):
+        self.ctx = ctx
+        dev = ctx.torch_device
+        self.dim = d = 2 if hasattr(problem.mesh, "tris") else 3
+        X = np.asarray(problem.mesh.xy if d == 2 else problem.mesh.xyz, np.float64)
+        cells = problem.mesh.tris if d == 2 else problem.mesh.tets
+        (gbp.setup_problem_2d if d == 2 else gbp.setup_problem)(ctx, problem)
+        self.B, self.K = B, K = len(starts), starts[0].K
+        self.cf = torch.from_numpy(np.tile(problem.cf.astype(np.float32), (B, 1))).to(dev)
+        self.ct = torch.from_numpy(np.tile(problem.ct.astype(np.float32), (B, 1))).to(dev)
+        idx = np.stack([o.idx for o in starts]).astype(np.int64)
+        bary = np.stack([o.bary for o in starts]).astype(np.float64)
+        V = X[cells[idx]]  # [B, K, d + 1, d]
+        M = np.concatenate([V.transpose(0, 1, 3, 2), np.ones((B, K, 1, d + 1))], axis=2)
+        self.Vt_inv = torch.tensor(np.linalg.inv(M), dtype=torch.float32, device=dev)
+        self.on_idx = torch.from_numpy(idx.astype(np.int32)).to(dev)
+        self.x = torch.tensor(np.einsum("bkq,bkqr->bkr", bary, V).astype(np.float32), device=dev,
+                              requires_grad=True)
+        self.t = torch.tensor(np.stack([o.t for o in starts]).astype(np.float32), device=dev, requires_grad=True)
+        self.target = torch.from_numpy(np.tile(np.asarray(target, np.float32)[None], (B, 1, 1))).to(dev)
+        self.tmpl = problem.tmpl
+        self.opts = opts if opts is not None else gbp.make_opts()
+        self.precision = precision
+        self.locator = None
+        if relocate:
+            from .relocate import SimplexLocator
+            self.locator = SimplexLocator(X, cells)
+        self.out = None
+
+    def bary(self):
+        xh = torch.cat([self.x.detach(), torch.ones_like(self.x[..., :1])], dim=-1)
+        return torch.einsum("bkij,bkj->bki", self.Vt_inv, xh).contiguous()
+
+    def evaluate(self):
+        """Losses [B]; the gradients land in the output dict."""
+        self.ctx.set_onsets_batch(gbp.ONSET_ELEMENT, self.on_idx, self.t.detach().contiguous(), self.bary())
+        self.out = self.ctx.forward_backward_batch(self.cf, self.ct, self.target, self.tmpl, opts=self.opts,
+                                                   precision=self.precision, out=self.out)
+        return self.out["loss"]
+
+    @torch.no_grad()
+    def project_positions(self, floor=1e-3):
+        d = self.dim
+        if self.locator is not None:
+            from .relocate import relocate_onsets
+            relocate_onsets(self.locator, self.x.view(-1, d), self.on_idx.view(-1),
+                            self.Vt_inv.view(-1, d + 1, d + 1), floor=floor)
+            return
+        b = self.bary().clamp_min(floor)
+        b = b / b.sum(dim=-1, keepdim=True)
+        Minv = self.Vt_inv
+        # x = V b with V the first d rows of M = inverse(Minv)
+        self.x.copy_(torch.einsum("bkrq,bkq->bkr", torch.linalg.inv(Minv)[:, :, :d, :], b))
+
+    def run_adam(self, iters=400, lr=0.5, log_every=0):
+        opt = torch.optim.Adam([self.x, self.t], lr=lr)
+        hist = []
+        t_start = time.perf_counter()
+        for it in range(iters):
+            loss = self.evaluate()
+            self.x.grad = self.out["d_x"]
+            self.t.grad = self.out["d_t"]
+            opt.step()
+            self.project_positions()
+            if log_every and (it % log_every == 0 or it == iters - 1):
+                hist.append((it, float(loss.min().item()), time.perf_counter() - t_start))
+        torch.cuda.synchronize()
+        return hist, time.perf_counter() - t_start
+
+
+def run_2d(iters: int = 400, lr: float = 0.5, n_init: int = 8, starts: int = 1, device: int = 0,
+           log_every: int = 20, relocate: bool = True, log=print):
+    """The paper's 2-D simulation study (Sec. III-A), on synthetic geometry.
+    Ground truth: 4 sites with times in [2.5, 10] ms on the 0.45 mm LV slice
+    (10,440 vertices), its ECG from that mesh's lead field.  Model: the
+    0.9 mm slice (2,700 vertices, 7 leads) with the true velocities, starting
+    from n_init sites at 0 ms spread evenly on the mid-wall circle.  Adam on
+    the sites' positions and times, 400 epochs at lr 0.5 as in the paper.
+    starts > 1 runs that many starts at once (the ring turned by a fraction
+    of its spacing each; start 0 is the single start) and keeps the one
+    with the lowest misfit.  Reports the steady-state time per epoch, the
+    misfit, and the RMSE of the activation times against the ground truth at
+    the coarse vertices (which coincide with fine ones), also for the true
+    sites on the coarse mesh (the floor the coarse model itself sets)."""
+    import dataclasses as dc
+
+    from . import synth as S
+    ctx = gbp.Context(device)
+    dev = ctx.torch_device
+    fine = S.make_2d_torso(fine=True)
+    gbp.setup_problem_2d(ctx, fine)
+    phi_f, _, _ = ctx.eikonal_solve()
+    target = ctx.ecg_forward(phi_f, fine.tmpl).cpu().numpy()
+    phi_true = torch.from_numpy(phi_f.cpu().numpy().reshape(29, 360)[::2, ::2].reshape(-1)).to(dev)
+    coarse = S.make_2d_torso(fine=False)
+    target_d = torch.from_numpy(target).to(dev)
+
+    def ring(offset):
+        ang = offset + 2 * np.pi * np.arange(n_init) / n_init
+        idx, bary = S.locate_2d(coarse.mesh, 24.5 * np.stack([np.cos(ang), np.sin(ang)], axis=1))
+        return S.Onsets(S.ONSET_ELEMENT, idx.astype(np.int32), np.zeros(n_init, np.float32),
+                        bary.astype(np.float32))
+
+    cf_d = torch.from_numpy(coarse.cf).to(dev)
+    ct_d = torch.from_numpy(coarse.ct).to(dev)
+
+    @torch.no_grad()
+    def evaluate_sites(idx, t, bary):
+        """(misfit, activation RMSE vs truth) of one site set on the coarse mesh."""
+        ctx.set_velocities(cf_d, ct_d)
+        ctx.set_onsets(gbp.ONSET_ELEMENT, idx.contiguous(), t.contiguous(), bary.contiguous())
+        phi, _, _ = ctx.eikonal_solve()
+        V = ctx.ecg_forward(phi, coarse.tmpl)
+        loss, _ = ctx.ecg_loss_backward(phi, V, target_d, coarse.tmpl)
+        d = (phi - phi_true).double()
+        return float(loss.item()), float(torch.sqrt((d * d).mean()).item())
+
+    tr = coarse.onsets
+    if starts == 1:
+        p0 = dc.replace(coarse, onsets=ring(0.0), onset_t=np.zeros(n_init, np.float32))
+        inv = InverseProblem(ctx, p0, target, optimise_velocities=False, relocate=relocate)
+        loss0, rmse0 = evaluate_sites(inv.op.on_idx, inv.t.detach(), inv.bary())
+        hist, wall = inv.run_adam(iters=iters, lr=lr, log_every=log_every)
+        loss1, rmse1 = evaluate_sites(inv.op.on_idx, inv.t.detach(), inv.bary())
+        x, t = inv.x.detach().cpu().numpy(), inv.t.detach().cpu().numpy()
+        extra = {}
+    else:
+        ms = MultiStartInverse(ctx, coarse, target, [ring(2 * np.pi * s / (n_init * starts)) for s in range(starts)],
+                               relocate=relocate)
+        loss0, rmse0 = evaluate_sites(ms.on_idx[0], ms.t[0].detach(), ms.bary()[0])
+        hist, wall = ms.run_adam(iters=iters, lr=lr, log_every=log_every)
+        losses = ms.evaluate().cpu().numpy()
+        best = int(np.argmin(losses))
+        b_all = ms.bary()
+        loss1, rmse1 = evaluate_sites(ms.on_idx[best], ms.t[best].detach(), b_all[best])
+        first = evaluate_sites(ms.on_idx[0], ms.t[0].detach(), b_all[0])
+        x, t = ms.x[best].detach().cpu().numpy(), ms.t[best].detach().cpu().numpy()
+        extra = dict(starts=starts, best_start=best, start_losses=[float(v) for v in losses],
+                     start0_loss=first[0], start0_act_rmse_ms=first[1])
+    floor = evaluate_sites(torch.from_numpy(tr.idx).to(dev), torch.from_numpy(tr.t).to(dev),
+                           torch.from_numpy(tr.bary).to(dev))
+    true_pts = np.einsum("kq,kqr->kr", tr.bary.astype(np.float64),
+                         coarse.mesh.xy.astype(np.float64)[coarse.mesh.tris[tr.idx]])
+    res = dict(workload=f"2-D LV slice, {coarse.mesh.n_v} vertices ({coarse.mesh.n_t} triangles), "
+                        f"{coarse.L.shape[0]} leads, T={coarse.tmpl.T}; truth on the {fine.mesh.n_v}-vertex slice "
+                        f"with {tr.K} sites; {n_init} initial sites at 0 ms",
+               iters=iters, lr=lr, wall_s=wall,
+               ms_per_epoch=(1e3 * (hist[-1][2] - hist[0][2]) / max(hist[-1][0] - hist[0][0], 1)
+                             if len(hist) > 1 else 1e3 * wall / max(iters, 1)),
+               loss0=loss0, loss_final=loss1, act_rmse_ms=(rmse0, rmse1),
+               true_sites_loss=floor[0], true_sites_act_rmse_ms=floor[1], **extra,
+               sites_final=[[float(a), float(b), float(c)] for (a, b), c in zip(x, t)],
+               sites_true=[[float(a), float(b), float(c)] for (a, b), c in zip(true_pts, tr.t)],
+               history=hist)
+    for it, l, tt in hist:
+        log(f"epoch {it:4d}  loss {l:.6g}  {tt:.2f} s")
+    ctx.close()
+    return res
+
+
 if __name__ == "__main__":
     import argparse
     import json
 
-    ap = argparse.ArgumentParser(description="Adam inverse loop on the 72^3 cube")
-    ap.add_argument("--iters", type=int, default=500)
-    ap.add_argument("--lr", type=float, default=1e-2)
+    ap = argparse.ArgumentParser(description="Adam inverse loops: the 72^3 cube, or the 2-D LV-slice study")
+    ap.add_argument("--study", choices=["c3", "2d"], default="c3")
+    ap.add_argument("--iters", type=int, default=0, help="0: 500 (c3) / 400 (2d)")
+    ap.add_argument("--lr", type=float, default=0.0, help="0: 1e-2 (c3) / 0.5 (2d)")
     ap.add_argument("--n", type=int, default=72)
+    ap.add_argument("--starts", type=int, default=1, help="2d: starts run together in one batch")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
-    r = run_c3(iters=a.iters, lr=a.lr, n=a.n)
+    if a.study == "2d":
+        r = run_2d(iters=a.iters or 400, lr=a.lr or 0.5, starts=a.starts)
+    else:
+        r = run_c3(iters=a.iters or 500, lr=a.lr or 1e-2, n=a.n)
     print(json.dumps({k: v for k, v in r.items() if k != "history"}))
     if a.out:
         with open(a.out, "w") as f:

@@ -619,8 +619,8 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
     rng = np.random.default_rng(seed + 3)
     loc = None
     if relocate:
-        from .relocate import TetLocator
-        loc = TetLocator(c5.problem.mesh.xyz, c5.problem.mesh.tets)
+        from .relocate import SimplexLocator
+        loc = SimplexLocator(c5.problem.mesh.xyz, c5.problem.mesh.tets)
     rows = []
     for i in range(n_eval):
         truth = Pv[i]

@@ -33,6 +33,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "Onsets", "Template", "Problem", "TriMesh", "Problem2D", "make_2d",
+    "lv_slice", "lead_field_2d", "locate_2d", "make_2d_torso",
     "kuhn_cube", "voxel_kuhn", "biv_shell_mask",
     "fibres_cube", "fibres_biv", "smooth_field", "nodal_to_tet_mean",
     "fibonacci_sphere", "torso_electrodes", "lead_field", "twelve_lead_matrix",
@@ -584,6 +585,8 @@ class Problem2D:
     onset_t: np.ndarray      # float32 [K]
     L: np.ndarray     # float32 [N, n_v]
     tmpl: Template
+    onsets: Onsets | None = None  # element onsets (idx = triangles, bary [K, 3]); None: the nodal ones above
+    extra: dict = dataclasses.field(default_factory=dict)
 
 
 def tri_square(n: int, side: float = 10.0, jitter: float = 0.0, seed: int = 0) -> TriMesh:
@@ -633,3 +636,120 @@ def make_2d(n: int = 40, seed: int = 0, side: float = 10.0, n_leads: int = 7, K:
     L -= L.mean(axis=1, keepdims=True)
     L *= 100.0 / mesh.n_v
     return Problem2D("2d", mesh, fib, cf, ct, nodes, t, L.astype(np.float32), Template(-80.0, 20.0, 1.0, 0.0, 1.0, T))
+
+
+def lv_slice(n_r: int = 15, n_theta: int = 180, r_in: float = 18.0, r_out: float = 31.0) -> TriMesh:
+    """Annular left-ventricular slice: n_r rings from r_in to r_out (mm),
+    n_theta vertices per ring, each cell split into two counter-clockwise
+    triangles (alternating diagonals).  The default has 2,700 vertices and a
+    spacing of about 0.9 mm, the size of the paper's 2-D study; (2 n_r - 1,
+    2 n_theta) gives the half-spacing mesh whose even vertices coincide with
+    these."""
+    r = np.linspace(r_in, r_out, n_r)
+    th = 2 * np.pi * np.arange(n_theta) / n_theta
+    R, TH = np.meshgrid(r, th, indexing="ij")  # [n_r, n_theta]
+    xy = np.stack([R * np.cos(TH), R * np.sin(TH)], axis=-1).reshape(-1, 2)
+    tris = []
+    for i in range(n_r - 1):
+        for j in range(n_theta):
+            a, b = i * n_theta + j, i * n_theta + (j + 1) % n_theta
+            c, d = (i + 1) * n_theta + (j + 1) % n_theta, (i + 1) * n_theta + j
+            # (radius, angle) is positively oriented: a -> d -> c is counter-clockwise
+            if (i + j) % 2 == 0:
+                tris += [(a, c, b), (a, d, c)]
+            else:
+                tris += [(a, d, b), (b, d, c)]
+    return TriMesh(xy.astype(np.float32), np.asarray(tris, np.int32))
+
+
+def lead_field_2d(mesh: TriMesh, electrodes: np.ndarray, combos: np.ndarray | None = None) -> np.ndarray:
+    """2-D counterpart of lead_field: L_l = K Z_l with K the P1 stiffness
+    matrix of the triangle mesh (unit conductivity) and Z_l(x) =
+    -ln|x - e_l| / (2 pi) the infinite-plane lead field, assembled per
+    triangle as L_l[a] += area * grad(lambda_a) . grad(Z_h)."""
+    x = mesh.xy.astype(np.float64)
+    E = np.asarray(electrodes, float)
+    Z = -np.log(np.linalg.norm(x[None, :, :] - E[:, None, :], axis=2)) / (2 * np.pi)
+    t = mesh.tris
+    v = x[t]  # [n_t, 3, 2]
+    J = (v[:, 1:] - v[:, :1]).transpose(0, 2, 1)
+    area = 0.5 * np.linalg.det(J)
+    Jinv = np.linalg.inv(J)
+    g = np.concatenate([-Jinv.sum(axis=1, keepdims=True), Jinv], axis=1)  # [n_t, 3, 2]
+    L = np.zeros((E.shape[0], mesh.n_v))
+    for e in range(E.shape[0]):
+        gz = np.einsum("cai,ca->ci", g, Z[e][t])
+        contrib = area[:, None] * np.einsum("cai,ci->ca", g, gz)
+        L[e] = np.bincount(t.ravel(), weights=contrib.ravel(), minlength=mesh.n_v)
+    if combos is not None:
+        L = np.asarray(combos, float) @ L
+    return L.astype(np.float32)
+
+
+def locate_2d(mesh: TriMesh, pts: np.ndarray):
+    """(triangle, barycentric coordinates) of each point, by brute force."""
+    v = mesh.xy.astype(np.float64)[mesh.tris]
+    J = (v[:, 1:] - v[:, :1]).transpose(0, 2, 1)
+    idx, bary = [], []
+    for p in np.asarray(pts, float):
+        lam = np.linalg.solve(J, (p - v[:, 0])[..., None])[..., 0]
+        b = np.concatenate([1 - lam.sum(axis=1, keepdims=True), lam], axis=1)
+        j = int(np.argmax(b.min(axis=1)))
+        bj = np.clip(b[j], 0, 1)
+        idx.append(j)
+        bary.append(bj / bj.sum())
+    return np.asarray(idx), np.asarray(bary)
+
+
+def make_2d_torso(fine: bool = False, seed: int = 0, K: int = 4, T: int = 200, perturb: float = 0.0,
+                  onsets: Onsets | None = None) -> Problem2D:
+    """The paper's 2-D simulation study, synthetic (its torso geometry and
+    conductivities are not given): the LV slice of lv_slice (0.9 mm, 2,700
+    vertices; fine=True: 0.45 mm, 10,440 vertices), fibres along the local
+    circumferential direction turned from -60 deg (epicardium) to +60 deg
+    (endocardium), c_f = 0.6 / c_t = 0.3 mm/ms (times a smooth factor
+    exp(+-perturb) around the ring when perturb > 0), 8 electrodes on a
+    60 mm circle around a torso centre 10 mm left of the slice, electrodes 0
+    and 1 (the arms) forming Wilson's central terminal, 7 leads (the 6 others
+    against it, and lead I = e1 - e0), T samples at 1 ms.  Sites: K element
+    onsets in the half y > 2 mm with times U[2.5, 10] ms, drawn on the coarse
+    mesh and located on the fine one, unless given."""
+    coarse = lv_slice()
+    mesh = lv_slice(29, 360) if fine else coarse
+    xy = mesh.xy.astype(np.float64)
+    cen = xy[mesh.tris].mean(axis=1)
+    rad = np.linalg.norm(cen, axis=1)
+    tang = np.stack([-cen[:, 1], cen[:, 0]], axis=1) / rad[:, None]
+    ang = np.deg2rad(-60.0 + 120.0 * (31.0 - rad) / (31.0 - 18.0))
+    c, s_ = np.cos(ang), np.sin(ang)
+    fib = np.stack([c * tang[:, 0] - s_ * tang[:, 1], s_ * tang[:, 0] + c * tang[:, 1]], axis=1)
+    cf = np.full(mesh.n_t, 0.6)
+    ct = np.full(mesh.n_t, 0.3)
+    if perturb > 0:
+        r = np.random.default_rng(seed + 99)
+        ph = r.uniform(0, 2 * np.pi, 4)
+        th = np.arctan2(cen[:, 1], cen[:, 0])
+        cf *= np.exp(perturb * (0.6 * np.sin(2 * th + ph[0]) + 0.4 * np.sin(3 * th + ph[1])))
+        ct *= np.exp(perturb * (0.6 * np.sin(2 * th + ph[2]) + 0.4 * np.cos(3 * th + ph[3])))
+    if onsets is None:
+        rng = np.random.default_rng(seed)
+        ccen = coarse.xy.astype(np.float64)[coarse.tris].mean(axis=1)
+        pool = np.nonzero(ccen[:, 1] > 2.0)[0]
+        idx = rng.choice(pool, size=K, replace=False)
+        b = 0.1 + 0.7 * rng.dirichlet(np.ones(3), size=K)
+        t = rng.uniform(2.5, 10.0, size=K)
+        if fine:
+            pts = np.einsum("kq,kqr->kr", b, coarse.xy.astype(np.float64)[coarse.tris[idx]])
+            idx, b = locate_2d(mesh, pts)
+        onsets = Onsets(ONSET_ELEMENT, idx.astype(np.int32), t.astype(np.float32), b.astype(np.float32))
+    th = 2 * np.pi * (np.arange(8) + 0.5) / 8 + np.pi / 2
+    el = np.array([-10.0, 0.0]) + 60.0 * np.stack([np.cos(th), np.sin(th)], axis=1)
+    combos = np.zeros((7, 8))
+    for q in range(6):
+        combos[q, q + 2] = 1.0
+        combos[q, :2] = -0.5
+    combos[6, 1], combos[6, 0] = 1.0, -1.0
+    L = lead_field_2d(mesh, el, combos)
+    return Problem2D("2d_torso_fine" if fine else "2d_torso", mesh, fib.astype(np.float32),
+                     cf.astype(np.float32), ct.astype(np.float32), np.zeros(0, np.int32), onsets.t, L,
+                     Template(-80.0, 20.0, 1.0, 0.0, 1.0, T), onsets=onsets)

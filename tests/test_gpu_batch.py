@@ -114,3 +114,60 @@ def test_batch_errors(ctx):
     st = lib.gbp_forward_backward_batch(ctx.h, 2, C.byref(o), C.byref(tm), 0, C.c_void_p(cfd.data_ptr()),
                                         C.c_void_p(ctd.data_ptr()), None, None, None, None, None, None, None, None)
     assert st == 1  # no target / loss
+
+
+def test_batch_with_per_problem_sites(ctx):
+    """gbp_set_onsets_batch: each problem of the batch has its own element
+    sites (different tets and barycentric points) and times; every problem
+    equals the oracle and the single-problem entry point on its own sites.
+    A later batch with another B is refused until gbp_set_onsets."""
+    B = 3
+    p, cf, ct, t, _ = batch_problem(10, B, seed=4)
+    sites = [S.onsets_element(p.mesh, 3, seed=40 + b, tmin=0.0, tmax=6.0) for b in range(B)]
+    tg = []
+    for b in range(B):
+        ons = S.Onsets(S.ONSET_ELEMENT, sites[b].idx, t[b], sites[b].bary)
+        ek = O.eikonal(p.mesh, p.fib, (cf[b] * 1.05).astype(np.float32), ct[b], ons)
+        tg.append(S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 70 + b).astype(np.float32))
+    tg = np.stack(tg)
+    gbp.setup_problem(ctx, p)
+    idx = np.stack([s.idx for s in sites])
+    bary = np.stack([s.bary for s in sites])
+    ctx.set_onsets_batch(S.ONSET_ELEMENT, dev(idx, np.int32), dev(t), dev(bary))
+    out = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl)  # times from set_onsets_batch
+    assert ctx.stats()["status"] == 0
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    for b in range(B):
+        ons = S.Onsets(S.ONSET_ELEMENT, sites[b].idx, t[b], sites[b].bary)
+        ref = O.forward_backward(p.mesh, p.fib, cf[b], ct[b], ons, p.L, p.tmpl, tg[b])
+        ambiguous = bool(np.any(ref["margin"] <= 1e-5 * np.maximum(1.0, ref["phi"])))
+        tol = 1e-2 if ambiguous else 1e-3
+        assert abs(g["loss"][b] - ref["loss"]) / ref["loss"] < 1e-4, b
+        for k in ("d_cf", "d_ct", "d_t", "d_x"):
+            assert rel_l2(g[k][b], ref[k]) < tol, (b, k, rel_l2(g[k][b], ref[k]))
+    with pytest.raises(RuntimeError):
+        ctx.forward_backward_batch(dev(cf[:2]), dev(ct[:2]), dev(tg[:2]), p.tmpl)
+    for b in range(B):
+        ctx.set_onsets(S.ONSET_ELEMENT, dev(sites[b].idx, np.int32), dev(t[b]), dev(sites[b].bary))
+        one = ctx.forward_backward(dev(cf[b]), dev(ct[b]), dev(tg[b]), p.tmpl)
+        assert abs(one["loss"].item() - g["loss"][b]) <= 1e-5 * g["loss"][b]
+        for k in ("d_cf", "d_ct", "d_t", "d_x"):
+            assert rel_l2(g[k][b], one[k].cpu().numpy()) < 1e-4, (b, k)
+
+
+def test_batch_without_times_uses_the_shared_ones(ctx):
+    """t = NULL in the batched call: every problem takes the times of
+    gbp_set_onsets, also when the call first grows the batch."""
+    p, cf, ct, t, tg = batch_problem(8, 4, seed=6)
+    fresh = gbp.Context(0)
+    try:
+        gbp.setup_problem(fresh, p)
+        a = fresh.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl)
+        a = {k: v.cpu().numpy() for k, v in a.items()}
+        tt = np.repeat(p.onsets.t[None], 4, axis=0)
+        b = fresh.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(tt))
+        assert fresh.stats()["status"] == 0
+        for k in ("loss", "d_cf", "d_t", "d_x"):
+            assert rel_l2(a[k], b[k].cpu().numpy()) < 1e-5, k
+    finally:
+        fresh.close()
