@@ -396,9 +396,11 @@ def main():
 
 
 def kernel_hash() -> str:
+    """Hash of the FIM kernel's sources (the kernel and its device header): a
+    stored ncu traffic figure applies only while it matches."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("fim.cu", "gbp_internal.cuh"):
+    for f in ("fim.cu", "gbp_device.cuh"):
         with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]

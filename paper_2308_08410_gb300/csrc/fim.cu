@@ -1,6 +1,7 @@
-// fim.cu -- eikonal solve: per-tet metric precompute, onset seeding, the
-// persistent active-list Fast Iterative Method (Algorithm 2 with the local
-// solver of Sec. II-B) and the parent pass.
+// fim.cu -- the persistent active-list Fast Iterative Method (Algorithm 2
+// with the local solver of Sec. II-B): one cooperative kernel that runs
+// every iteration of the solve.  The kernels around it (per-tet precompute,
+// onset seeding, parent pass) are in fim_aux.cu.
 #include "gbp_internal.cuh"
 
 namespace gbp {
@@ -10,200 +11,6 @@ namespace gbp {
 // which the chaotic relaxation of Algorithm 2 tolerates).
 #define FIM_LD(p) __ldcg(p)
 
-// vertices of the face of tet tv opposite slot s, in increasing slot order
-__device__ __forceinline__ void face_ids(int4 tv, int s, int &vi, int &f0, int &f1, int &f2)
-{
-    vi = s == 0 ? tv.x : s == 1 ? tv.y : s == 2 ? tv.z : tv.w;
-    f0 = s == 0 ? tv.y : tv.x;
-    f1 = s <= 1 ? tv.z : tv.y;
-    f2 = s <= 2 ? tv.w : tv.z;
-}
-
-// transformed edge vectors p_n = R (v_{j_n} - v_i) of face (tet tv, opposite slot s)
-__device__ __forceinline__ void face_vectors(const float4 *__restrict__ xyz, int4 tv, int s, float4 m, float sd,
-                                             float3 p[3], int fv[3])
-{
-    int vi, f0, f1, f2;
-    face_ids(tv, s, vi, f0, f1, f2);
-    fv[0] = f0;
-    fv[1] = f1;
-    fv[2] = f2;
-    const float4 xi = __ldg(&xyz[vi]);
-    const float4 x0 = __ldg(&xyz[f0]), x1 = __ldg(&xyz[f1]), x2 = __ldg(&xyz[f2]);
-    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
-    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
-    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
-}
-
-// ---------------------------------------------------------------------------
-// per-tet metric (Sec. II-A): R = D^{1/2} in factored form
-// ---------------------------------------------------------------------------
-// Batched: entry g = b * n_t + j of the per-problem arrays (cf, ct, tm, tsd).
-__global__ void k_precompute(int64_t n_t, int64_t n_tot, const float *__restrict__ fib, const float *__restrict__ cf,
-                             const float *__restrict__ ct, float4 *__restrict__ tm, float *__restrict__ tsd,
-                             Control *ctl)
-{
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= n_tot) return;
-    const int64_t j = g % n_t;
-    float fx = fib[3 * j], fy = fib[3 * j + 1], fz = fib[3 * j + 2];
-    float nn = sqrtf(fx * fx + fy * fy + fz * fz);
-    float vf = cf[g], vt = ct[g];
-    bool bad = !(nn > 0.f) || !(vf > 0.f) || !(vt > 0.f) || !isfinite(vf) || !isfinite(vt) || !isfinite(nn);
-    if (bad) {
-        atomicCAS(&ctl->param_status, 0, (int)GBP_ERR_NOT_SPD);
-        nn = 1.f; fx = 1.f; fy = fz = 0.f;
-        vf = vt = 1.f;
-    }
-    float in = 1.f / nn;
-    float sa = 1.f / vt;
-    tm[g] = make_float4(fx * in, fy * in, fz * in, sa);
-    tsd[g] = 1.f / vf - sa;
-}
-
-cudaError_t launch_precompute(gbp_ctx *c)
-{
-    int th = 256;
-    const int64_t n_tot = c->n_t * c->nb;
-    int64_t bl = (n_tot + th - 1) / th;
-    k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->fib, c->cf, c->ct, c->tm, c->tsd, c->ctl);
-    c->launches++;
-    return cudaGetLastError();
-}
-
-__global__ void k_lipschitz(int64_t n_t, int64_t n_tot, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
-                            const float4 *__restrict__ tm, const float *__restrict__ tsd, float4 *__restrict__ tlip)
-{
-    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g >= n_tot) return;
-    int4 tv = tets[g % n_t];
-    float4 m = tm[g];
-    float sd = tsd[g];
-    float L[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        float3 p[3];
-        int fv[3];
-        face_vectors(xyz, tv, s, m, sd, p, fv);
-        L[s] = face_lipschitz(p);
-    }
-    tlip[g] = make_float4(L[0], L[1], L[2], L[3]);
-}
-
-cudaError_t launch_lipschitz(gbp_ctx *c)
-{
-    int th = 256;
-    const int64_t n_tot = c->n_t * c->nb;
-    int64_t bl = (n_tot + th - 1) / th;
-    k_lipschitz<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->xyz, c->tets, c->tm, c->tsd, c->tlip);
-    c->launches++;
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// onset seeding (Algorithm 2 initialisation, Eq. upwind_xi)
-// ---------------------------------------------------------------------------
-
-// Batched: thread g = b * K + k (onset times t [nb][K]; sites shared, or
-// one set per problem when per_problem is set: idx [nb][K], bary [nb][K][4]).
-// Vertices from n_real on (the apex of a lifted triangle mesh) take no key.
-__global__ void k_onset_keys(int K, int nb, int per_problem, int kind, const int *__restrict__ idx,
-                             const float *__restrict__ bary,
-                             const float *__restrict__ t, int64_t n_v, int64_t n_real, int64_t n_t,
-                             const float4 *__restrict__ xyz,
-                             const int4 *__restrict__ tets, const float4 *__restrict__ tm,
-                             const float *__restrict__ tsd, unsigned long long *keys_all, Control *ctl)
-{
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= K * nb) return;
-    const int b = g / K, k = g - b * K;
-    unsigned long long *keys = keys_all + (int64_t)b * n_v;
-    const float tk = t[g];
-    const int sk = per_problem ? g : k;
-    int id = idx[sk];
-    if (kind == GBP_ONSET_NODAL) {
-        if (id < 0 || id >= n_real) {
-            atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
-            return;
-        }
-        unsigned long long key = ((unsigned long long)float_key(tk) << 32) | (unsigned)k;
-        atomicMin(&keys[id], key);
-    } else {
-        if (id < 0 || id >= n_t) {
-            atomicCAS(&ctl->status, 0, (int)GBP_ERR_INVALID_ARG);
-            return;
-        }
-        int4 tv = tets[id];
-        int ids[4] = {tv.x, tv.y, tv.z, tv.w};
-        float4 x[4];
-        float3 xo = make_float3(0.f, 0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            x[q] = xyz[ids[q]];
-            float b = bary[4 * sk + q];
-            xo.x = fmaf(b, x[q].x, xo.x);
-            xo.y = fmaf(b, x[q].y, xo.y);
-            xo.z = fmaf(b, x[q].z, xo.z);
-        }
-        float4 m = tm[(int64_t)b * n_t + id];
-        float sd = tsd[(int64_t)b * n_t + id];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            float3 w = xform(make_float3(x[q].x - xo.x, x[q].y - xo.y, x[q].z - xo.z), m, sd);
-            float v = tk + sqrtf(f3dot(w, w));
-            unsigned long long key = ((unsigned long long)float_key(v) << 32) | (unsigned)k;
-            if (ids[q] < n_real) atomicMin(&keys[ids[q]], key);
-        }
-    }
-}
-
-// Per vertex: decode the onset key, reset the FIM state.
-__global__ void k_init_nodes(int64_t n_v, const unsigned long long *__restrict__ keys, float *phi, int4 *rec,
-                             int *chg, int *stamp, int2 *pc)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_v) return;
-    unsigned long long key = keys[i];
-    if (key != ~0ull) {
-        phi[i] = key_float((unsigned int)(key >> 32));
-        rec[i] = make_int4(-1 - (int)(key & 0xffffffffu), 0, 0, 0);
-        chg[i] = 0;
-    } else {
-        phi[i] = GBP_INF;
-        rec[i] = make_int4(GBP_UNREACHED, 0, 0, 0);
-        chg[i] = -1000000;
-    }
-    stamp[i] = 0;
-    pc[i] = make_int2(__float_as_int(phi[i]), chg[i]);
-}
-
-// phi of every vertex entry from the FIM's packed (value, change stamp) state
-__global__ void k_unpack_pc(int64_t n_tot, const int2 *__restrict__ pc, float *phi)
-{
-    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g < n_tot) phi[g] = __int_as_float(pc[g].x);
-}
-
-// Seeded vertices put their neighbours on the first active list.
-// Batched: vertex entry g = b * n_v + i (lists hold such entries).
-__global__ void k_seed_lists(int n_v, int n_tot, const unsigned long long *__restrict__ keys,
-                             const int *__restrict__ n2n_ptr, const int *__restrict__ n2n, int *stamp, int *list1,
-                             Control *ctl)
-{
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_tot || keys[g] == ~0ull) return;
-    const int b = g / n_v, i = g - b * n_v;
-    for (int e = n2n_ptr[i]; e < n2n_ptr[i + 1]; ++e) {
-        const int m = b * n_v + n2n[e];
-        if (atomicMax(&stamp[m], 1) < 1) {
-            int pos = atomicAdd(&ctl->count[1], 1);
-            list1[pos] = m;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// persistent FIM (Algorithm 2)
 // ---------------------------------------------------------------------------
 struct FimArgs {
     int64_t n_v;    // vertices per problem
@@ -479,24 +286,10 @@ static int fim_grid(gbp_ctx *c, const void *fn)
 
 cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
 {
-    cudaError_t err;
+    cudaError_t err = launch_fim_seed(c);
+    if (err) return err;
     const int64_t n_v = c->n_v;
     const int64_t n_tot = n_v * c->nb;  // all problems of the batch (< 2^31, checked at set-up)
-    // reset the control block (counters, status) and the onset keys; the
-    // precompute's status word (last field) is kept
-    err = cudaMemsetAsync(c->ctl, 0, offsetof(Control, param_status), c->stream);
-    if (err) return err;
-    err = cudaMemsetAsync(c->keys, 0xff, sizeof(unsigned long long) * n_tot, c->stream);
-    if (err) return err;
-    int th = 256;
-    k_onset_keys<<<(c->K * c->nb + th - 1) / th, th, 0, c->stream>>>(c->K, c->nb, c->site_b > 0,
-                                                                      c->onset_kind, c->on_idx,
-                                                                      c->on_bary, c->on_t, n_v, c->n_e, c->n_t, c->xyz,
-                                                                      c->tets, c->tm, c->tsd, c->keys, c->ctl);
-    unsigned bl = (unsigned)((n_tot + th - 1) / th);
-    k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp, c->pc);
-    c->launches += 2;
-    if ((err = cudaGetLastError())) return err;
     long long *trace = nullptr;
     if (c->trace_on) {
         if (c->trace_cap < o->max_iters + 2) {
@@ -511,11 +304,6 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
             trace = c->trace;
         }
     }
-    k_seed_lists<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->keys, c->n2n_ptr, c->n2n, c->stamp,
-                                           c->lists + n_tot, c->ctl);
-    c->launches++;
-    if ((err = cudaGetLastError())) return err;
-
     FimArgs a;
     a.n_v = n_v;
     a.n_t = c->n_t;
@@ -550,137 +338,7 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     time_end(c, 0);
     c->launches++;
     if (err) return err;
-    k_unpack_pc<<<bl, th, 0, c->stream>>>(n_tot, c->pc, c->phi);
-    c->launches++;
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// parent pass: alpha of the final parent face with the final values
-// ---------------------------------------------------------------------------
-// Batched: entry g = b * n_v + i.  Outputs (single problem only) and the
-// unreached count cover the caller's vertices i < n_e; for a lifted triangle
-// mesh (dim 2) the code is written as triangle * 3 + slot and alpha as the
-// weights of the triangle's two other vertices (the apex weight is 0).
-template <int MODE>
-__global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t, const float4 *__restrict__ xyz,
-                              const int4 *__restrict__ tets, const float4 *__restrict__ tm_all,
-                              const float *__restrict__ tsd_all, const float4 *__restrict__ tlip_all, int n_f,
-                              const float *__restrict__ phi_all, int4 *rec, float *out_phi, int32_t *out_parent,
-                              float *out_alpha, Control *ctl)
-{
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= n_tot) return;
-    const int b = g / n_v;
-    const float *phi = phi_all + (int64_t)b * n_v;
-    const float4 *tm = tm_all + (int64_t)b * n_t;
-    const float *tsd = tsd_all + (int64_t)b * n_t;
-    const float4 *tlip = tlip_all + (int64_t)b * n_t;
-    const int i = g;
-    int4 r = rec[i];
-    int code = r.x;
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-    float pv = phi_all[i];
-    if (code >= 0) {
-        int j = code >> 2, s = code & 3;
-        int4 tv = tets[j];
-        float3 p[3];
-        int fv[3];
-        face_vectors(xyz, tv, s, tm[j], tsd[j], p, fv);
-        float ph[3] = {phi[fv[0]], phi[fv[1]], phi[fv[2]]};
-        LocalRes lr;
-        int fb = 0;
-        if (MODE == GBP_LOCAL_FISTA) {
-            float4 Lq = tlip[j];
-            float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
-            lr = local_fista(p, ph, Lv, n_f);
-        } else {
-            lr = local_exact(p, ph, &fb);
-        }
-        a0 = lr.a0;
-        a1 = lr.a1;
-        a2 = lr.a2;
-        rec[i] = make_int4(code, __float_as_int(a0), __float_as_int(a1), __float_as_int(a2));
-    }
-    if (i - b * n_v >= n_e) return;
-    if (code == GBP_UNREACHED) atomicAdd(&ctl->unreached, 1ull);
-    if (out_phi) out_phi[i] = pv;
-    if (dim == 2) {
-        if (out_parent) out_parent[i] = code >= 0 ? (code >> 2) * 3 + (code & 3) : code;
-        if (out_alpha) {
-            out_alpha[2 * i] = a0;
-            out_alpha[2 * i + 1] = a1;
-        }
-        return;
-    }
-    if (out_parent) out_parent[i] = code;
-    if (out_alpha) {
-        out_alpha[3 * i] = a0;
-        out_alpha[3 * i + 1] = a1;
-        out_alpha[3 * i + 2] = a2;
-    }
-}
-
-cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_t *parent, float *alpha)
-{
-    int th = 256;
-    const int n_tot = (int)(c->n_v * c->nb);
-    unsigned bl = (unsigned)((n_tot + th - 1) / th);
-    time_begin(c, 1);
-    if (mode == GBP_LOCAL_FISTA)
-        k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
-                                                                 c->xyz, c->tets, c->tm, c->tsd, c->tlip, n_f,
-                                                                 c->phi, c->rec, phi, parent, alpha, c->ctl);
-    else
-        k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
-                                                                 c->xyz, c->tets, c->tm, c->tsd, c->tlip, n_f,
-                                                                 c->phi, c->rec, phi, parent, alpha, c->ctl);
-    time_end(c, 1);
-    c->launches++;
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// local problems on independent faces (diagnostic entry point)
-// ---------------------------------------------------------------------------
-__global__ void k_local_batch(int64_t n, const float *__restrict__ e, const float *__restrict__ fib,
-                              const float *__restrict__ cf, const float *__restrict__ ct,
-                              const float *__restrict__ Phi, int mode, int n_f, float *value, float *alpha,
-                              Control *ctl)
-{
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float fx = fib[3 * i], fy = fib[3 * i + 1], fz = fib[3 * i + 2];
-    float in = rsqrtf(fx * fx + fy * fy + fz * fz);
-    float sa = 1.f / ct[i];
-    float4 m = make_float4(fx * in, fy * in, fz * in, sa);
-    float sd = 1.f / cf[i] - sa;
-    float3 p[3];
-    float ph[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        p[a] = xform(make_float3(e[9 * i + 3 * a], e[9 * i + 3 * a + 1], e[9 * i + 3 * a + 2]), m, sd);
-        ph[a] = Phi[3 * i + a];
-    }
-    LocalRes r;
-    int fb = 0;
-    if (mode == GBP_LOCAL_FISTA) r = local_fista(p, ph, face_lipschitz(p), n_f);
-    else r = local_exact(p, ph, &fb);
-    if (fb) atomicAdd(&ctl->fp64_fallbacks, (unsigned long long)fb);
-    value[i] = r.v;
-    alpha[3 * i] = r.a0;
-    alpha[3 * i + 1] = r.a1;
-    alpha[3 * i + 2] = r.a2;
-}
-
-cudaError_t launch_local_batch(gbp_ctx *c, int64_t n, const float *e, const float *fib, const float *cf,
-                               const float *ct, const float *Phi, int mode, int n_f, float *value, float *alpha)
-{
-    int th = 128;
-    unsigned bl = (unsigned)((n + th - 1) / th);
-    k_local_batch<<<bl, th, 0, c->stream>>>(n, e, fib, cf, ct, Phi, mode, n_f, value, alpha, c->ctl);
-    c->launches++;
-    return cudaGetLastError();
+    return launch_unpack_state(c);
 }
 
 }  // namespace gbp
