@@ -128,8 +128,14 @@ class InverseProblem:
         V = torch.from_numpy(self.X.astype(np.float32)).to(self.x.device)[self.tets[self.op.on_idx.long()]]
         self.x.copy_(torch.einsum("kq,kqr->kr", b, V))
 
-    def run_adam(self, iters=500, lr=1e-2, log_every=0, callback=None):
-        opt = torch.optim.Adam(self.params(), lr=lr)
+    def run_adam(self, iters=500, lr=1e-2, log_every=0, callback=None, lr_sites=None):
+        """Adam at lr; onset times and positions at lr_sites when given."""
+        if lr_sites is None:
+            opt = torch.optim.Adam(self.params(), lr=lr)
+        else:
+            site = [p for p in (self.t, self.x) if p.requires_grad]
+            rest = [p for p in self.params() if all(p is not q for q in site)]
+            opt = torch.optim.Adam([{"params": rest, "lr": lr}, {"params": site, "lr": lr_sites}])
         hist = []
         t_start = time.perf_counter()
         for it in range(iters):
@@ -155,18 +161,19 @@ class VertexLogToTet(torch.autograd.Function):
 
     @staticmethod
     def forward(fctx, logc, tets):
-        c = torch.exp(logc[tets].mean(dim=1))
+        # logc [n_v] or [B, n_v] -> c [n_t] or [B, n_t]
+        c = torch.exp(logc[..., tets].mean(dim=-1))
         fctx.save_for_backward(c, tets)
-        fctx.n = logc.shape[0]
+        fctx.shape = logc.shape
         return c
 
     @staticmethod
     def backward(fctx, g):
         c, tets = fctx.saved_tensors
         nw = tets.shape[1]
-        w = (g * c / nw).unsqueeze(1).expand(-1, nw).reshape(-1)
-        out = torch.zeros(fctx.n, dtype=g.dtype, device=g.device)
-        out.index_add_(0, tets.reshape(-1), w)
+        w = (g * c / nw).unsqueeze(-1).expand(*c.shape, nw)
+        out = torch.zeros(fctx.shape, dtype=g.dtype, device=g.device)
+        out.index_add_(out.dim() - 1, tets.reshape(-1), w.reshape(*c.shape[:-1], -1))
         return out, None
 
 
@@ -199,61 +206,92 @@ class GeodesicEcgLoss(torch.autograd.Function):
 
 
 def run_c3(iters: int = 500, lr: float = 1e-2, n: int = 72, device: int = 0, log_every: int = 25,
-           precision: int = gbp.PREC_FP32, log=print):
+           precision: int = gbp.PREC_FP32, init: str = "surface", starts: int = 1, lr_sites: float | None = 5e-2,
+           log=print):
     """The inverse loop on the 72^3 cube (2.15M tets): Adam on the per-vertex
     log-velocity fields and the 10 onset times / positions, from the
     prior-mean start (c_f = 0.6, c_t = 0.3 mm/ms everywhere, onset times
-    10 ms, onsets at the centroids of the true onset tets: relocation across
-    elements is not modelled).  Target: the ground-truth ECG plus 5 % noise.
-    Returns the loss history and the activation-time error against the
-    ground truth before and after."""
+    10 ms).  init = "surface": 10 random sites on the mesh surface, which
+    relocation walks through the mesh; init = "centroids": the centroids of
+    the true onset tets (an informed start).  starts > 1 (surface init only)
+    runs that many independent surface draws together in one batch and
+    keeps the start with the lowest misfit.  lr_sites: learning rate of the
+    onset times (ms) and positions (mm) (None: lr).  Target: the
+    ground-truth ECG plus 5 % noise.  Returns the loss history and the
+    activation-time error against the ground truth before and after."""
     from . import synth as S
     p = S.make_c3(n=n)
     ctx = gbp.Context(device)
-    dp = gbp.setup_problem(ctx, p)
+    gbp.setup_problem(ctx, p)
     phi_true, _, _ = ctx.eikonal_solve()
     V = ctx.ecg_forward(phi_true, p.tmpl).cpu().numpy()
     phi_true = phi_true.clone()
     target = S.add_noise(V, p.extra["noise"], 4242)
     ons = p.onsets
-    cent = np.full((ons.K, 4), 0.25, np.float32)
-    p0 = S.Problem(p.name, p.mesh, p.fib, p.cf, p.ct, S.Onsets(ons.kind, ons.idx, ons.t, cent), p.L, p.tmpl,
-                   p.extra)
-    inv = InverseProblem(ctx, p0, target, precision=precision, init_t=np.full(ons.K, 10.0, np.float32))
-    del dp
+    t10 = np.full(ons.K, 10.0, np.float32)
+    if init == "surface":
+        draws = [S.onsets_surface(p.mesh, ons.K, seed=777 + s_, tmin=10.0, tmax=10.0) for s_ in range(starts)]
+    elif init == "centroids" and starts == 1:
+        draws = [S.Onsets(ons.kind, ons.idx, t10, np.full((ons.K, 4), 0.25, np.float32))]
+    else:
+        raise ValueError(f"unsupported init {init!r} with {starts} starts")
 
-    def act_err():
-        with torch.no_grad():
-            cf, ct = inv.tet_velocities()
-            ctx.set_velocities(cf.contiguous(), ct.contiguous())
-            ctx.set_onsets(inv.kind, inv.op.on_idx, inv.t.detach().contiguous(), inv.bary())
-            phi, _, _ = ctx.eikonal_solve()
-            d = (phi - phi_true).double()
-            return float(torch.sqrt((d * d).mean()).item()), float(d.abs().max().item())
+    @torch.no_grad()
+    def act_err(log_cf, log_ct, on_idx, t, bary):
+        cells = torch.from_numpy(p.mesh.tets.astype(np.int64)).to(ctx.torch_device)
+        ctx.set_velocities(VertexLogToTet.apply(log_cf, cells).contiguous(),
+                           VertexLogToTet.apply(log_ct, cells).contiguous())
+        ctx.set_onsets(gbp.ONSET_ELEMENT, on_idx.contiguous(), t.contiguous(), bary.contiguous())
+        phi, _, _ = ctx.eikonal_solve()
+        d = (phi - phi_true).double()
+        return float(torch.sqrt((d * d).mean()).item()), float(d.abs().max().item())
 
-    rmse0, max0 = act_err()
-    loss0 = float(inv.loss().item())
-    hist, wall = inv.run_adam(iters=iters, lr=lr, log_every=log_every,
-                              callback=None)
-    rmse1, max1 = act_err()
-    lcf_true = torch.from_numpy(p.extra["log_cf_nodal"]).to(inv.log_cf.device)
-    lct_true = torch.from_numpy(p.extra["log_ct_nodal"]).to(inv.log_ct.device)
+    extra = {}
+    if starts == 1:
+        p0 = S.Problem(p.name, p.mesh, p.fib, p.cf, p.ct, draws[0], p.L, p.tmpl, p.extra)
+        inv = InverseProblem(ctx, p0, target, precision=precision, init_t=t10)
+        state = lambda: (inv.log_cf.detach(), inv.log_ct.detach(), inv.op.on_idx, inv.t.detach(),  # noqa: E731
+                         inv.bary())
+        rmse0, max0 = act_err(*state())
+        loss0 = float(inv.loss().item())
+        hist, wall = inv.run_adam(iters=iters, lr=lr, log_every=log_every, lr_sites=lr_sites)
+        loss1 = hist[-1][1] if hist else loss0
+        rmse1, max1 = act_err(*state())
+        lcf, lct, t_fit = inv.log_cf.detach(), inv.log_ct.detach(), inv.t.detach().cpu().numpy()
+    else:
+        ms = MultiStartInverse(ctx, p, target, draws, precision=precision, optimise_velocities=True)
+        b0 = ms.bary()
+        rmse0, max0 = act_err(ms.log_cf[0].detach(), ms.log_ct[0].detach(), ms.on_idx[0], ms.t[0].detach(), b0[0])
+        loss0 = float(ms.evaluate()[0].item())
+        hist, wall = ms.run_adam(iters=iters, lr=lr, log_every=log_every, lr_sites=lr_sites)
+        losses = ms.evaluate().detach().cpu().numpy()
+        best = int(np.argmin(losses))
+        loss1 = float(losses[best])
+        bb = ms.bary()
+        rmse1, max1 = act_err(ms.log_cf[best].detach(), ms.log_ct[best].detach(), ms.on_idx[best],
+                              ms.t[best].detach(), bb[best])
+        first = act_err(ms.log_cf[0].detach(), ms.log_ct[0].detach(), ms.on_idx[0], ms.t[0].detach(), bb[0])
+        lcf, lct, t_fit = ms.log_cf[best].detach(), ms.log_ct[best].detach(), ms.t[best].detach().cpu().numpy()
+        extra = dict(starts=starts, best_start=best, start_losses=[float(v) for v in losses],
+                     start0_loss=float(losses[0]), start0_act_rmse_ms=first[0])
+    lcf_true = torch.from_numpy(p.extra["log_cf_nodal"]).to(lcf.device)
+    lct_true = torch.from_numpy(p.extra["log_ct_nodal"]).to(lct.device)
     res = dict(workload=f"{n}^3 cube, {p.mesh.n_t} tets, {ons.K} element onsets, {p.L.shape[0]} leads, "
                         f"T={p.tmpl.T}, 5% noise",
-               iters=iters, lr=lr, wall_s=wall,
+               init=init, iters=iters, lr=lr, lr_sites=lr_sites if lr_sites is not None else lr, wall_s=wall,
                # steady state: the first iteration also loads the torch kernels
                ms_per_iter=(1e3 * (hist[-1][2] - hist[0][2]) / max(hist[-1][0] - hist[0][0], 1)
                             if len(hist) > 1 else 1e3 * wall / max(iters, 1)),
-               loss0=loss0, loss_final=hist[-1][1] if hist else loss0, noise_floor=float(
-                   np.mean((target - V) ** 2)),
+               loss0=loss0, loss_final=loss1, noise_floor=float(np.mean((target - V) ** 2)),
                act_rmse_ms=(rmse0, rmse1), act_max_ms=(max0, max1),
-               log_cf_mae=float((inv.log_cf.detach() - lcf_true).abs().mean().item()),
-               log_ct_mae=float((inv.log_ct.detach() - lct_true).abs().mean().item()),
+               log_cf_mae=float((lcf - lcf_true).abs().mean().item()),
+               log_ct_mae=float((lct - lct_true).abs().mean().item()),
                log_cf_mae0=float((np.log(0.6) - lcf_true).abs().mean().item()),
                log_ct_mae0=float((np.log(0.3) - lct_true).abs().mean().item()),
-               t_err_ms=(float(np.abs(10.0 - ons.t).mean()),
-                         float(np.abs(inv.t.detach().cpu().numpy() - ons.t).mean())),
-               history=hist)
+               # onset k starts in true onset k's tet only for the centroid start
+               t_err_ms=((float(np.abs(10.0 - ons.t).mean()), float(np.abs(t_fit - ons.t).mean()))
+                         if init == "centroids" else None),
+               **extra, history=hist)
     for it, l, tt in hist:
         log(f"iter {it:4d}  loss {l:.6g}  {tt:.2f} s")
     ctx.close()
@@ -261,16 +299,18 @@ def run_c3(iters: int = 500, lr: float = 1e-2, n: int = 72, device: int = 0, log
 
 
 class MultiStartInverse:
-    """B starts of the site fit run together (Sec. IV: batched optimisation
-    as the way out of local minima).  Adam on every start's element-onset
-    positions and times ([B, K, d], [B, K]) with the velocities fixed; each
-    epoch is one batched evaluation (gbp_set_onsets_batch, then
+    """B starts of the inverse problem run together (Sec. IV: batched
+    optimisation as the way out of local minima).  Adam on every start's
+    element-onset positions and times ([B, K, d], [B, K]) and, with
+    optimise_velocities, its per-vertex log-velocity fields ([B, n_v], mapped
+    to elements as in InverseProblem); otherwise the problem's velocities are
+    kept.  Each epoch is one batched evaluation (gbp_set_onsets_batch, then
     gbp_forward_backward_batch: the FIM, parent pass and adjoint of all
     starts share their launches).  The starts stay independent: each loss
     depends on its own start only and Adam acts elementwise."""
 
     def __init__(self, ctx: gbp.Context, problem, target: np.ndarray, starts, opts=None, precision=gbp.PREC_FP32,
-                 relocate=True):
+                 relocate=True, optimise_velocities=False, init_log_cf=np.log(0.6), init_log_ct=np.log(0.3)):
         self.ctx = ctx
         dev = ctx.torch_device
         self.dim = d = 2 if hasattr(problem.mesh, "tris") else 3
@@ -280,6 +320,12 @@ class MultiStartInverse:
         self.B, self.K = B, K = len(starts), starts[0].K
         self.cf = torch.from_numpy(np.tile(problem.cf.astype(np.float32), (B, 1))).to(dev)
         self.ct = torch.from_numpy(np.tile(problem.ct.astype(np.float32), (B, 1))).to(dev)
+        self.optimise_velocities = optimise_velocities
+        if optimise_velocities:
+            n_v = problem.mesh.n_v
+            self.cells = torch.from_numpy(cells.astype(np.int64)).to(dev)
+            self.log_cf = torch.full((B, n_v), float(init_log_cf), device=dev, requires_grad=True)
+            self.log_ct = torch.full((B, n_v), float(init_log_ct), device=dev, requires_grad=True)
         idx = np.stack([o.idx for o in starts]).astype(np.int64)
         bary = np.stack([o.bary for o in starts]).astype(np.float64)
         V = X[cells[idx]]  # [B, K, d + 1, d]
@@ -304,11 +350,25 @@ class MultiStartInverse:
         return torch.einsum("bkij,bkj->bki", self.Vt_inv, xh).contiguous()
 
     def evaluate(self):
-        """Losses [B]; the gradients land in the output dict."""
+        """Losses [B]; the gradients land in the output dict (and, with
+        optimise_velocities, in log_cf.grad / log_ct.grad)."""
+        if self.optimise_velocities:
+            cf = VertexLogToTet.apply(self.log_cf, self.cells)
+            ct = VertexLogToTet.apply(self.log_ct, self.cells)
+            self.cf, self.ct = cf.detach().contiguous(), ct.detach().contiguous()
         self.ctx.set_onsets_batch(gbp.ONSET_ELEMENT, self.on_idx, self.t.detach().contiguous(), self.bary())
         self.out = self.ctx.forward_backward_batch(self.cf, self.ct, self.target, self.tmpl, opts=self.opts,
                                                    precision=self.precision, out=self.out)
+        if self.optimise_velocities:
+            self.log_cf.grad = self.log_ct.grad = None
+            torch.autograd.backward([cf, ct], [self.out["d_cf"], self.out["d_ct"]])
         return self.out["loss"]
+
+    def params(self, lr, lr_sites=None):
+        groups = [{"params": [self.x, self.t], "lr": lr if lr_sites is None else lr_sites}]
+        if self.optimise_velocities:
+            groups.append({"params": [self.log_cf, self.log_ct], "lr": lr})
+        return groups
 
     @torch.no_grad()
     def project_positions(self, floor=1e-3):
@@ -324,8 +384,8 @@ class MultiStartInverse:
         # x = V b with V the first d rows of M = inverse(Minv)
         self.x.copy_(torch.einsum("bkrq,bkq->bkr", torch.linalg.inv(Minv)[:, :, :d, :], b))
 
-    def run_adam(self, iters=400, lr=0.5, log_every=0):
-        opt = torch.optim.Adam([self.x, self.t], lr=lr)
+    def run_adam(self, iters=400, lr=0.5, log_every=0, lr_sites=None):
+        opt = torch.optim.Adam(self.params(lr, lr_sites))
         hist = []
         t_start = time.perf_counter()
         for it in range(iters):
@@ -439,13 +499,16 @@ if __name__ == "__main__":
     ap.add_argument("--iters", type=int, default=0, help="0: 500 (c3) / 400 (2d)")
     ap.add_argument("--lr", type=float, default=0.0, help="0: 1e-2 (c3) / 0.5 (2d)")
     ap.add_argument("--n", type=int, default=72)
-    ap.add_argument("--starts", type=int, default=1, help="2d: starts run together in one batch")
+    ap.add_argument("--starts", type=int, default=1, help="starts run together in one batch")
+    ap.add_argument("--init", choices=["surface", "centroids"], default="surface", help="c3: initial sites")
+    ap.add_argument("--lr-sites", type=float, default=5e-2, help="c3: learning rate of onset times / positions")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
     if a.study == "2d":
         r = run_2d(iters=a.iters or 400, lr=a.lr or 0.5, starts=a.starts)
     else:
-        r = run_c3(iters=a.iters or 500, lr=a.lr or 1e-2, n=a.n)
+        r = run_c3(iters=a.iters or 500, lr=a.lr or 1e-2, n=a.n, init=a.init, starts=a.starts,
+                   lr_sites=a.lr_sites)
     print(json.dumps({k: v for k, v in r.items() if k != "history"}))
     if a.out:
         with open(a.out, "w") as f:
