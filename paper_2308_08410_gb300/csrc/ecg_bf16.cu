@@ -23,6 +23,9 @@
 
 namespace gbp {
 
+#ifndef GBP_BF16_CTAS_PER_SM
+#define GBP_BF16_CTAS_PER_SM 6  // CTAs per SM of the split-K grid (128 threads, 36 KB of stages each)
+#endif
 constexpr int BF_M = 128;   // samples per tile (MMA M)
 constexpr int BF_N = 16;    // leads (MMA N)
 constexpr int BF_KT = 64;   // vertices per pipeline stage
@@ -251,7 +254,7 @@ cudaError_t launch_ecg_forward_bf16(gbp_ctx *c, const float *phi, const gbp_temp
 {
     const int N = c->N, T = t->T;
     const int mtiles = (T + BF_M - 1) / BF_M;
-    int nsplit = (4 * c->num_sms + mtiles - 1) / mtiles;
+    int nsplit = (GBP_BF16_CTAS_PER_SM * c->num_sms + mtiles - 1) / mtiles;
     int64_t per = (c->n_e + nsplit - 1) / nsplit;
     per = ((per + BF_KT - 1) / BF_KT) * BF_KT;
     nsplit = (int)((c->n_e + per - 1) / per);

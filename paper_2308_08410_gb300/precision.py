@@ -100,10 +100,15 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser(description="BF16 vs FP32 ECG precision study")
     ap.add_argument("--n", type=int, default=100)
     ap.add_argument("--iters", type=int, default=100)
+    ap.add_argument("--only", choices=["c4", "c2"], default=None, help="run one of the two studies")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
     t0 = time.perf_counter()
-    r = {"c4": run_c4(a.n), "c2_trajectory": run_c2_trajectory(a.iters)}
+    r = {}
+    if a.only in (None, "c4"):
+        r["c4"] = run_c4(a.n)
+    if a.only in (None, "c2"):
+        r["c2_trajectory"] = run_c2_trajectory(a.iters)
     r["wall_s"] = time.perf_counter() - t0
     s = json.dumps(r)
     print(s)
