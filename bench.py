@@ -267,24 +267,20 @@ def main():
         total_s = float(tt.item())
         dist.barrier()
 
-    # e2e: the same evaluation from host buffers through gbp_forward_backward_host
+    # e2e: the same evaluation from host buffers through the host entry points
+    # (gbp_forward_backward_batch_host / gbp_forward_backward_host)
     e2e = None
     if not args.no_e2e and B > 1:
-        # the batch through the same entry point, inputs copied from pinned
-        # host memory and outputs read back inside the timed region
-        hin = [torch.from_numpy(a).pin_memory() for a in (cfB_np, ctB_np, tB_np, tgB_np)]
-        din = [torch.empty_like(h, device=dev) for h in hin]
-        outs = ("loss", "d_cf", "d_ct", "d_t", "d_x")
+        # inputs copied from pinned host memory and outputs written back to
+        # pinned host memory inside the call, every step
+        hin = [torch.from_numpy(a).pin_memory().numpy() for a in (cfB_np, ctB_np, tB_np, tgB_np)]
+        n_t_, K_ = cfB_np.shape[1], tB_np.shape[1]
+        shapes = dict(loss=(B,), d_cf=(B, n_t_), d_ct=(B, n_t_), d_t=(B, K_), d_x=(B, K_, 3))
+        hout = {k: torch.empty(v, dtype=torch.float32).pin_memory().numpy() for k, v in shapes.items()}
 
         def e2e_step():
-            nonlocal out
-            for h, d in zip(hin, din):
-                d.copy_(h, non_blocking=True)
-            out = ctx.forward_backward_batch(din[0], din[1], din[3], p.tmpl, t=din[2], opts=opts, precision=prec,
-                                             out=out)
-            res = [out[k].to("cpu", non_blocking=True) for k in outs]
-            torch.cuda.synchronize()
-            return res
+            return ctx.forward_backward_batch_host(hin[0], hin[1], hin[3], p.tmpl, t=hin[2], opts=opts,
+                                                   precision=prec, out=hout)
 
         for _ in range(2):
             e2e_step()
@@ -299,8 +295,8 @@ def main():
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
             e2e_s = float(tt.item())
         e2e = {"value": world * B * args.steps / e2e_s, "unit": "evals/s",
-               "h2d_bytes_per_step": int(sum(h.numel() * 4 for h in hin)),
-               "d2h_bytes_per_step": int(sum(out[k].numel() * 4 for k in outs))}
+               "h2d_bytes_per_step": int(sum(h.nbytes for h in hin)),
+               "d2h_bytes_per_step": int(sum(h.nbytes for h in hout.values()))}
     if not args.no_e2e and B == 1:
         h_out = None
         for _ in range(2):

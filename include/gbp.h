@@ -274,6 +274,20 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *ctx, int32_t B, const gbp_solve_o
                                       float *loss, float *ecg, float *d_cf, float *d_ct, float *d_t,
                                       float *d_x);
 
+/* gbp_forward_backward_batch from HOST buffers: the inputs are copied
+ * host->device from the caller's arrays and the outputs device->host into
+ * them inside the call, which synchronises.  cf, ct host [B][n_t]; t host
+ * [B][K] (NULL: as in gbp_forward_backward_batch); target host [B][N][T];
+ * loss host [B]; d_cf, d_ct host [B][n_t]; d_t host [B][K]; d_x host
+ * [B][K][d] (outputs may be NULL).  The copies run straight from and to the
+ * caller's memory: page-locked (pinned) host memory gives the full link
+ * bandwidth, pageable memory works at the driver's staged rate.  Device
+ * staging buffers are owned by the context.  Errors as the batched call. */
+gbp_status gbp_forward_backward_batch_host(gbp_ctx *ctx, int32_t B, const gbp_solve_opts *opts,
+                                           const gbp_template *tmpl, int32_t precision, const float *cf,
+                                           const float *ct, const float *t, const float *target,
+                                           float *loss, float *d_cf, float *d_ct, float *d_t, float *d_x);
+
 /* ------------------------------------------------------------------ */
 /* learned initialiser: network training and inference kernels          */
 /* ------------------------------------------------------------------ */

@@ -237,6 +237,8 @@ void gbp_destroy(gbp_ctx *c)
     dfree(&c->ecg_tmp);
     dfree(&c->dev_in);
     dfree(&c->dev_out);
+    dfree(&c->bat_in);
+    dfree(&c->bat_out);
     dfree(&c->loss_buf);
     dfree(&c->trace);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
@@ -903,6 +905,48 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opt
     c->solve_gen = -1;
     c->param_gen++;
     return from_cuda(e);
+}
+
+gbp_status gbp_forward_backward_batch_host(gbp_ctx *c, int32_t B, const gbp_solve_opts *opts,
+                                           const gbp_template *tmpl, int32_t precision, const float *cf,
+                                           const float *ct, const float *t, const float *target, float *loss,
+                                           float *d_cf, float *d_ct, float *d_t, float *d_x)
+{
+    if (!c || B < 1 || !cf || !ct || !target || !valid_template(tmpl)) return GBP_ERR_INVALID_ARG;
+    if (!c->n_v || !c->has_fib || !c->K || !c->N) return GBP_ERR_STATE;
+    DeviceGuard g(c->device);
+    const int64_t n_t = c->n_t, K = c->K, NT = (int64_t)c->N * tmpl->T, d = c->dim;
+    // device staging: in = [cf | ct | t | target], out = [loss | d_cf | d_ct | d_t | d_x], each [B][..]
+    const int64_t in_n = B * (2 * n_t + K + NT), out_n = B * (1 + 2 * n_t + (1 + d) * K);
+    cudaError_t e = cudaSuccess;
+    if (in_n > c->bat_in_cap) {
+        e = dalloc(&c->bat_in, in_n);
+        c->bat_in_cap = e ? 0 : in_n;
+    }
+    if (!e && out_n > c->bat_out_cap) {
+        e = dalloc(&c->bat_out, out_n);
+        c->bat_out_cap = e ? 0 : out_n;
+    }
+    if (e) return from_cuda(e);
+    float *di = c->bat_in, *dcf = di, *dct = di + B * n_t, *dt = di + 2 * B * n_t, *dtg = dt + B * K;
+    float *dl = c->bat_out, *dcf_o = dl + B, *dct_o = dcf_o + B * n_t, *dt_o = dct_o + B * n_t,
+          *dx_o = dt_o + B * K;
+    const cudaMemcpyKind h2d = cudaMemcpyHostToDevice, d2h = cudaMemcpyDeviceToHost;
+    e = cudaMemcpyAsync(dcf, cf, sizeof(float) * B * n_t, h2d, c->stream);
+    if (!e) e = cudaMemcpyAsync(dct, ct, sizeof(float) * B * n_t, h2d, c->stream);
+    if (!e && t) e = cudaMemcpyAsync(dt, t, sizeof(float) * B * K, h2d, c->stream);
+    if (!e) e = cudaMemcpyAsync(dtg, target, sizeof(float) * B * NT, h2d, c->stream);
+    if (e) return from_cuda(e);
+    gbp_status st = gbp_forward_backward_batch(c, B, opts, tmpl, precision, dcf, dct, t ? dt : nullptr, dtg, dl,
+                                               nullptr, dcf_o, dct_o, dt_o, dx_o);
+    if (st) return st;
+    if (loss) e = cudaMemcpyAsync(loss, dl, sizeof(float) * B, d2h, c->stream);
+    if (!e && d_cf) e = cudaMemcpyAsync(d_cf, dcf_o, sizeof(float) * B * n_t, d2h, c->stream);
+    if (!e && d_ct) e = cudaMemcpyAsync(d_ct, dct_o, sizeof(float) * B * n_t, d2h, c->stream);
+    if (!e && d_t) e = cudaMemcpyAsync(d_t, dt_o, sizeof(float) * B * K, d2h, c->stream);
+    if (!e && d_x) e = cudaMemcpyAsync(d_x, dx_o, sizeof(float) * B * d * K, d2h, c->stream);
+    if (e) return from_cuda(e);
+    return latched(c);
 }
 
 gbp_status gbp_local_solve_batch(gbp_ctx *c, int64_t n, const float *e, const float *fib, const float *cf,

@@ -84,6 +84,8 @@ struct gbp_ctx {
     float *dev_in = nullptr, *dev_out = nullptr;
     float *pin_in = nullptr, *pin_out = nullptr;
     int64_t stage_in_cap = 0, stage_out_cap = 0;
+    float *bat_in = nullptr, *bat_out = nullptr;  // device staging of gbp_forward_backward_batch_host
+    int64_t bat_in_cap = 0, bat_out_cap = 0;
     // timing
     bool timing = false;
     double ms[8] = {0};

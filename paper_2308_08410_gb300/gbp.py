@@ -95,6 +95,8 @@ def load():
                                        P, P, P], i32),
         "gbp_forward_backward_batch": ([P, i32, C.POINTER(SolveOpts), C.POINTER(Template), i32, P, P, P, P, P,
                                         P, P, P, P, P], i32),
+        "gbp_forward_backward_batch_host": ([P, i32, C.POINTER(SolveOpts), C.POINTER(Template), i32, P, P, P, P,
+                                             P, P, P, P, P], i32),
         "gbp_local_solve_batch": ([P, i64, P, P, P, P, P, i32, i32, P, P], i32),
         "gbp_enable_timing": ([P, i32], i32),
         "gbp_get_kernel_times": ([P, i32, P, P], i32),
@@ -130,7 +132,7 @@ def exported_symbols():
         "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
         "gbp_set_onsets", "gbp_set_onsets_batch", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
-        "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_local_solve_batch", "gbp_enable_timing",
+        "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_forward_backward_batch_host", "gbp_local_solve_batch", "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
         "gbp_ecg_forward_noalloc", "gbp_enable_trace", "gbp_get_trace",
         "gbp_nn_gemm_bf16", "gbp_nn_im2col", "gbp_nn_im2col_t", "gbp_nn_col2im", "gbp_nn_bias_act",
@@ -351,6 +353,25 @@ class Context:
                                                   _hptr(out["loss"]), _hptr(out["d_cf"]),
                                                   _hptr(out["d_ct"]), _hptr(out["d_t"]),
                                                   _hptr(out["d_x"])), "gbp_forward_backward_host")
+        return out
+
+    def forward_backward_batch_host(self, cf: np.ndarray, ct: np.ndarray, target: np.ndarray, tmpl,
+                                    t: np.ndarray | None = None, opts=None, precision=PREC_FP32, out=None):
+        """The batched evaluation from host arrays (cf, ct [B, n_t], target
+        [B, N, T], t [B, K] or None); outputs into host arrays.  Pinned
+        arrays (e.g. numpy views of pinned torch tensors) copy fastest."""
+        B = int(cf.shape[0])
+        if out is None:
+            out = dict(loss=np.zeros(B, np.float32), d_cf=np.empty((B, self.n_t), np.float32),
+                       d_ct=np.empty((B, self.n_t), np.float32), d_t=np.empty((B, self.K), np.float32),
+                       d_x=np.empty((B, self.K, self.dim), np.float32))
+        tm = make_template(tmpl)
+        o = opts if opts is not None else make_opts()
+        _check(self.lib.gbp_forward_backward_batch_host(self.h, B, C.byref(o), C.byref(tm), int(precision),
+                                                        _hptr(cf), _hptr(ct), _hptr(t), _hptr(target),
+                                                        _hptr(out["loss"]), _hptr(out["d_cf"]),
+                                                        _hptr(out["d_ct"]), _hptr(out["d_t"]),
+                                                        _hptr(out["d_x"])), "gbp_forward_backward_batch_host")
         return out
 
     def local_solve_batch(self, e, fib, cf, ct, phi, mode=LOCAL_EXACT, n_f=32):

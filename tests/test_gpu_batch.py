@@ -171,3 +171,23 @@ def test_batch_without_times_uses_the_shared_ones(ctx):
             assert rel_l2(a[k], b[k].cpu().numpy()) < 1e-5, k
     finally:
         fresh.close()
+
+
+def test_batch_host_entry_point(ctx):
+    """gbp_forward_backward_batch_host (host arrays in and out, copies inside
+    the call) equals the device-buffer batched call, from pageable and from
+    pinned host memory."""
+    B = 3
+    p, cf, ct, t, tg = batch_problem(9, B, seed=8)
+    gbp.setup_problem(ctx, p)
+    d = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(t))
+    d = {k: v.cpu().numpy() for k, v in d.items()}
+    for pinned in (False, True):
+        args = [cf, ct, tg, t]
+        if pinned:
+            args = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in args]
+        h = ctx.forward_backward_batch_host(args[0], args[1], args[2], p.tmpl, t=args[3])
+        assert ctx.stats()["status"] == 0
+        for k in ("loss", "d_cf", "d_ct", "d_t", "d_x"):
+            assert h[k].shape == d[k].shape, k
+            assert rel_l2(h[k], d[k]) < 1e-5, (pinned, k)
