@@ -65,6 +65,8 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->ct);
     dfree(&c->tm);
     dfree(&c->tsd);
+    dfree(&c->tf);
+    dfree(&c->tv);
     dfree(&c->tlip);
     dfree(&c->phi);
     dfree(&c->rec);
@@ -372,6 +374,8 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(dalloc(&c->ct, n_t));
     CK(dalloc(&c->tm, n_t));
     CK(dalloc(&c->tsd, n_t));
+    CK(dalloc(&c->tf, n_t));
+    CK(dalloc(&c->tv, n_t));
     CK(dalloc(&c->tlip, n_t));
     CK(dalloc(&c->phi, n_v));
     CK(dalloc(&c->rec, n_v));
@@ -800,6 +804,7 @@ static cudaError_t ensure_batch(gbp_ctx *c, int B)
     CK(dalloc(&c->ct, nt));
     CK(dalloc(&c->tm, nt));
     CK(dalloc(&c->tsd, nt));
+    CK(dalloc(&c->tv, nt));
     CK(dalloc(&c->tlip, nt));
     CK(dalloc(&c->phi, nv));
     CK(dalloc(&c->rec, nv));

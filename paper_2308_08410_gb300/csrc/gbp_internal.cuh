@@ -39,6 +39,8 @@ struct gbp_ctx {
     float *fib = nullptr, *cf = nullptr, *ct = nullptr;
     float4 *tm = nullptr;   // (fx, fy, fz, 1/ct)
     float *tsd = nullptr;   // 1/cf - 1/ct
+    float4 *tf = nullptr;   // unit fibre per tet (shared by the problems of a batch)
+    float2 *tv = nullptr;   // (1/ct, 1/cf - 1/ct) per tet and problem
     float4 *tlip = nullptr; // FISTA Lipschitz constants per (tet, slot)
     bool has_fib = false, has_vel = false, lip_valid = false;
     // onsets
