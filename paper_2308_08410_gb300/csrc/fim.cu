@@ -16,7 +16,6 @@ struct FimArgs {
     int64_t n_v;    // vertices per problem
     int64_t n_t;    // tets per problem
     int64_t n_tot;  // n_v x problems (entries of the active lists)
-    int64_t nb;     // problems
     const float4 *xyz;
     const int4 *tets;
     const float4 *tf;   // unit fibre per tet (shared by the batch)
@@ -125,18 +124,17 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             if (!__any_sync(0xffffffffu, act)) break;
 #endif
             // entry gi = b * n_v + i: vertex i of problem b
-            int gi = 0, i = 0, bb = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0, chg_old = 0;
+            int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0, chg_old = 0;
             int64_t toff = 0;
             float phi_old = 0.f;
             float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
             if (act) {
                 gi = __ldcg(&list[g]);
                 const int b = gi / (int)n_v;
-                bb = b;
                 boff = b * (int)n_v;
                 toff = (int64_t)b * a.n_t;
                 i = gi - boff;
-                const int2 own = FIM_LD(&a.pc[pc_index(b, i, n_v, a.nb)]);
+                const int2 own = FIM_LD(&a.pc[gi]);
                 phi_old = __int_as_float(own.x);
                 chg_old = own.y;
                 beg = __ldg(&a.n2t_ptr[i]);
@@ -167,9 +165,8 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
                     mk[r] = false;
                     ph[r][0] = ph[r][1] = ph[r][2] = GBP_INF;
                     if (fr[r].w >= 0) {
-                        const int2 q0 = FIM_LD(&a.pc[pc_index(bb, fr[r].x, n_v, a.nb)]),
-                                   q1 = FIM_LD(&a.pc[pc_index(bb, fr[r].y, n_v, a.nb)]),
-                                   q2 = FIM_LD(&a.pc[pc_index(bb, fr[r].z, n_v, a.nb)]);
+                        const int2 q0 = FIM_LD(&a.pc[boff + fr[r].x]), q1 = FIM_LD(&a.pc[boff + fr[r].y]),
+                                   q2 = FIM_LD(&a.pc[boff + fr[r].z]);
                         ph[r][0] = __int_as_float(q0.x);
                         ph[r][1] = __int_as_float(q1.x);
                         ph[r][2] = __int_as_float(q2.x);
@@ -184,7 +181,7 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
                     ++my_faces;
                     // metric: the fibre shared by the batch, the velocity terms of this problem
                     const float4 fj = __ldg(&a.tf[j]);
-                    const float2 vj = __ldg(&a.tv[tv_index(bb, j, a.n_t, a.nb)]);
+                    const float2 vj = __ldg(&a.tv[toff + j]);
                     const float4 m = make_float4(fj.x, fj.y, fj.z, vj.x);
                     const float sd = vj.y;
                     const float4 x0 = __ldg(&a.xyz[fr[r].x]), x1 = __ldg(&a.xyz[fr[r].y]),
@@ -222,7 +219,7 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
                 changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
                 if (sub == 0) {
                     // value and change stamp in one 8-byte store: readers see a pair
-                    a.pc[pc_index(bb, i, n_v, a.nb)] = make_int2(__float_as_int(best), changed ? k : chg_old);
+                    a.pc[gi] = make_int2(__float_as_int(best), changed ? k : chg_old);
                     a.rec[gi].x = best_code;
                 }
             }
@@ -314,7 +311,6 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     a.n_v = n_v;
     a.n_t = c->n_t;
     a.n_tot = n_tot;
-    a.nb = c->nb;
     a.xyz = c->xyz;
     a.tets = c->tets;
     a.tf = c->tf;

@@ -32,7 +32,7 @@ __global__ void k_precompute(int64_t n_t, int64_t n_tot, const float *__restrict
     tsd[g] = 1.f / vf - sa;
     // the FIM's compact copy: the fibre once per tet (shared by the batch),
     // the two velocity terms per problem
-    tv[tv_index(g / n_t, j, n_t, n_tot / n_t)] = make_float2(sa, 1.f / vf - sa);
+    tv[g] = make_float2(sa, 1.f / vf - sa);
     if (g < n_t) tf[g] = make_float4(fx * in, fy * in, fz * in, 0.f);
 }
 
@@ -134,8 +134,8 @@ __global__ void k_onset_keys(int K, int nb, int per_problem, int kind, const int
 }
 
 // Per vertex: decode the onset key, reset the FIM state.
-__global__ void k_init_nodes(int64_t n_tot, int64_t n_v1, int64_t nb, const unsigned long long *__restrict__ keys,
-                             float *phi, int4 *rec, int *chg, int *stamp, int2 *pc)
+__global__ void k_init_nodes(int64_t n_tot, const unsigned long long *__restrict__ keys, float *phi, int4 *rec,
+                             int *chg, int *stamp, int2 *pc)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_tot) return;
@@ -150,14 +150,14 @@ __global__ void k_init_nodes(int64_t n_tot, int64_t n_v1, int64_t nb, const unsi
         chg[i] = -1000000;
     }
     stamp[i] = 0;
-    pc[pc_index(i / n_v1, i % n_v1, n_v1, nb)] = make_int2(__float_as_int(phi[i]), chg[i]);
+    pc[i] = make_int2(__float_as_int(phi[i]), chg[i]);
 }
 
 // phi of every vertex entry from the FIM's packed (value, change stamp) state
-__global__ void k_unpack_pc(int64_t n_tot, int64_t n_v1, int64_t nb, const int2 *__restrict__ pc, float *phi)
+__global__ void k_unpack_pc(int64_t n_tot, const int2 *__restrict__ pc, float *phi)
 {
     const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (g < n_tot) phi[g] = __int_as_float(pc[pc_index(g / n_v1, g % n_v1, n_v1, nb)].x);
+    if (g < n_tot) phi[g] = __int_as_float(pc[g].x);
 }
 
 // Seeded vertices put their neighbours on the first active list.
@@ -199,7 +199,7 @@ cudaError_t launch_fim_seed(gbp_ctx *c)
                                                                       c->on_t, n_v, c->n_e, c->n_t, c->xyz,
                                                                       c->tets, c->tm, c->tsd, c->keys, c->ctl);
     const unsigned bl = (unsigned)((n_tot + th - 1) / th);
-    k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, n_v, c->nb, c->keys, c->phi, c->rec, c->chg, c->stamp, c->pc);
+    k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp, c->pc);
     k_seed_lists<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->keys, c->n2n_ptr, c->n2n, c->stamp,
                                            c->lists + n_tot, c->ctl);
     c->launches += 3;
@@ -210,7 +210,7 @@ cudaError_t launch_fim_seed(gbp_ctx *c)
 cudaError_t launch_unpack_state(gbp_ctx *c)
 {
     const int64_t n_tot = c->n_v * c->nb;
-    k_unpack_pc<<<(unsigned)((n_tot + 255) / 256), 256, 0, c->stream>>>(n_tot, c->n_v, c->nb, c->pc, c->phi);
+    k_unpack_pc<<<(unsigned)((n_tot + 255) / 256), 256, 0, c->stream>>>(n_tot, c->pc, c->phi);
     c->launches++;
     return cudaGetLastError();
 }

@@ -14,21 +14,6 @@
 
 namespace gbp {
 
-// Layout of the FIM's per-problem arrays in a batch of nb problems: the
-// packed vertex state pc and the per-tet velocity terms tv hold entry
-// (problem b, vertex or tet x) at b * n + x (problem-major; the
-// problem-minor layout x * nb + b measured 1.5-4 % slower at 8 problems).
-__host__ __device__ __forceinline__ int64_t pc_index(int64_t b, int64_t i, int64_t n_v, int64_t nb)
-{
-    (void)nb;
-    return b * n_v + i;
-}
-__host__ __device__ __forceinline__ int64_t tv_index(int64_t b, int64_t j, int64_t n_t, int64_t nb)
-{
-    (void)nb;
-    return b * n_t + j;
-}
-
 // ---------------------------------------------------------------------------
 // device control block (one per context)
 // ---------------------------------------------------------------------------
