@@ -157,12 +157,19 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
-def _hptr(a):
+def _hptr(a, dtype=None):
     if a is None:
         return None
     if not (isinstance(a, np.ndarray) and a.flags["C_CONTIGUOUS"]):
         raise ValueError("expected a C-contiguous numpy array")
+    if dtype is not None and a.dtype != dtype:
+        raise ValueError(f"expected a {np.dtype(dtype).name} array, got {a.dtype.name}")
     return a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a):
+    """Host pointer of a float32 array (the host entry points read float32)."""
+    return _hptr(a, np.float32)
 
 
 def make_opts(local_solver=LOCAL_EXACT, n_f=32, eps=0.0, max_iters=0) -> SolveOpts:
@@ -349,10 +356,10 @@ class Context:
         tm = make_template(tmpl)
         o = opts if opts is not None else make_opts()
         _check(self.lib.gbp_forward_backward_host(self.h, C.byref(o), C.byref(tm), int(precision),
-                                                  _hptr(cf), _hptr(ct), _hptr(t), _hptr(target),
-                                                  _hptr(out["loss"]), _hptr(out["d_cf"]),
-                                                  _hptr(out["d_ct"]), _hptr(out["d_t"]),
-                                                  _hptr(out["d_x"])), "gbp_forward_backward_host")
+                                                  _f32(cf), _f32(ct), _f32(t), _f32(target),
+                                                  _f32(out["loss"]), _f32(out["d_cf"]),
+                                                  _f32(out["d_ct"]), _f32(out["d_t"]),
+                                                  _f32(out["d_x"])), "gbp_forward_backward_host")
         return out
 
     def forward_backward_batch_host(self, cf: np.ndarray, ct: np.ndarray, target: np.ndarray, tmpl,
@@ -368,10 +375,10 @@ class Context:
         tm = make_template(tmpl)
         o = opts if opts is not None else make_opts()
         _check(self.lib.gbp_forward_backward_batch_host(self.h, B, C.byref(o), C.byref(tm), int(precision),
-                                                        _hptr(cf), _hptr(ct), _hptr(t), _hptr(target),
-                                                        _hptr(out["loss"]), _hptr(out["d_cf"]),
-                                                        _hptr(out["d_ct"]), _hptr(out["d_t"]),
-                                                        _hptr(out["d_x"])), "gbp_forward_backward_batch_host")
+                                                        _f32(cf), _f32(ct), _f32(t), _f32(target),
+                                                        _f32(out["loss"]), _f32(out["d_cf"]),
+                                                        _f32(out["d_ct"]), _f32(out["d_t"]),
+                                                        _f32(out["d_x"])), "gbp_forward_backward_batch_host")
         return out
 
     def local_solve_batch(self, e, fib, cf, ct, phi, mode=LOCAL_EXACT, n_f=32):
