@@ -43,7 +43,7 @@ struct AdjArgs {
     int K;
     const float4 *xyz;
     const int4 *tets;
-    const float4 *tm;
+    const float4 *tf;  // unit fibre per tet (shared by the batch)
     const float *tsd;
     const float *cf, *ct;
     const int4 *rec;
@@ -60,6 +60,7 @@ struct AdjArgs {
     int max_cycle_iters;
 };
 
+// m.xyz = unit fibre of the tet
 __device__ __forceinline__ void velocity_terms(float3 w, float4 m, float cfj, float ctj, float mu, float *d_cf,
                                                float *d_ct, int64_t j)
 {
@@ -98,7 +99,7 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, 
             w.z = fmaf(-al[q3], xq.z - xi.z, w.z);
             ++q3;
         }
-        velocity_terms(w, __ldg(&a.tm[toff + j]), __ldg(&a.cf[toff + j]), __ldg(&a.ct[toff + j]), m, a.d_cf, a.d_ct,
+        velocity_terms(w, __ldg(&a.tf[j]), __ldg(&a.cf[toff + j]), __ldg(&a.ct[toff + j]), m, a.d_cf, a.d_ct,
                        toff + j);
     } else if (code != GBP_UNREACHED) {
         const int k = -1 - code;
@@ -120,7 +121,7 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, 
                 w.y = fmaf(b, xi.y - xq.y, w.y);
                 w.z = fmaf(b, xi.z - xq.z, w.z);
             }
-            const float4 mm = __ldg(&a.tm[toff + E]);
+            const float4 mm = __ldg(&a.tf[E]);
             const float cfe = __ldg(&a.cf[toff + E]), cte = __ldg(&a.ct[toff + E]);
             float fw = mm.x * w.x + mm.y * w.y + mm.z * w.z;
             float3 wp = make_float3(w.x - fw * mm.x, w.y - fw * mm.y, w.z - fw * mm.z);
@@ -567,7 +568,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.K = c->K;
     a.xyz = c->xyz;
     a.tets = c->tets;
-    a.tm = c->tm;
+    a.tf = c->tf;
     a.tsd = c->tsd;
     a.cf = c->cf;
     a.ct = c->ct;
