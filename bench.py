@@ -4,7 +4,7 @@ tet-updates per second on the 72^3 Kuhn cube (373,248 vertices,
 2,147,466 tets), FP32 eikonal / ECG / adjoint on one GB300 per rank.
 
 One step = a batch of B forward-plus-gradient evaluations through the C ABI
-(gbp_forward_backward_batch; B = 8 starts of the inverse problem by
+(gbp_forward_backward_batch; B = 16 starts of the inverse problem by
 default, gbp_forward_backward when B = 1): per-tet metric precompute, onset
 seeding, the persistent FIM eikonal solve with parent record, the parent
 pass, the lead-field ECG (8 leads x 150 samples), the misfit and its
@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Geodesic-BP fwd+grad evals/s at 2.15M tets (72^3 Kuhn cube, FP32)"
-BATCH = 8                     # default problems per step (multi-start batch)
+BATCH = 16                    # default problems per step (multi-start batch)
 BYTES_PER_TET_UPDATE = 92.0   # algorithmic bytes per local face update
 BYTES_PER_ADJ_NODE = 130.0    # algorithmic bytes per vertex of the adjoint
 
@@ -341,7 +341,7 @@ def main():
                          "eikonal single-threaded, ECG / misfit OpenMP, SCC adjoint serial)",
                "seconds": t_cpu, "loss_gpu": float(out["loss"].reshape(-1)[0].item()), "loss_oracle": r["loss"]}
     traffic = None
-    prof = os.path.join(ROOT, "profiles", "fim_traffic_c3_batch8.txt")
+    prof = os.path.join(ROOT, "profiles", f"fim_traffic_c3_batch{B}.txt")
     if os.path.exists(prof):
         try:
             with open(prof) as f:
