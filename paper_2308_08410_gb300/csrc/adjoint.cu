@@ -593,6 +593,8 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.max_cycle_iters = 4096;
     // one 256-thread CTA per SM: ~39k threads, several times the widest
     // ready front, few enough that idle consumers poll lightly
+    // (2 or 4 per SM measured slower at 16 problems too: the consumers'
+    // polling contends with the pushes)
     int grid = c->num_sms;
     void *args[] = {&a};
     err = cudaLaunchCooperativeKernel((const void *)k_adjoint, dim3(grid), dim3(256), args, 0, c->stream);
