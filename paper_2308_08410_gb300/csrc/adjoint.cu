@@ -29,7 +29,13 @@
 // graph of the discrete fixed point can hold short cycles (non-causal
 // updates in anisotropic elements); the vertices they block are finished by
 // a bounded fixed-point (Jacobi) iteration on the remaining sub-graph, which
-// is closed under taking parents.
+// is closed under taking parents.  Most of those cycles are 2-cycles (c's
+// parent face holds p and p's holds c); they are solved exactly inside the
+// dataflow instead: the edge between the two is left out of their counts,
+// and once both have every other child, the second of the two to be ready
+// solves mu_c = S_c + a_pc mu_p, mu_p = S_p + a_cp mu_c (S = lambda plus the
+// other children's pushes) and carries on with both.  A pair caught in a
+// longer cycle never becomes ready and goes to the iteration as before.
 #include "gbp_internal.cuh"
 
 namespace gbp {
@@ -49,6 +55,9 @@ struct AdjArgs {
     const int4 *rec;
     int onset_kind;
     int site_per_problem;  // on_idx / on_bary hold one site set per problem
+    const int *pair;       // 2-cycle partner entry of each vertex entry, or -1
+    unsigned long long *pairw;  // hand-over word of each 2-cycle, at its smaller entry
+    int64_t qcap;          // 64-bit slots of the work queue
     const int *on_idx;
     const float *on_bary;
     const float *lam;
@@ -182,8 +191,68 @@ __global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const floa
     }
 }
 
+// weight of entry `target` in the parent face recorded in r (0 if absent)
+__device__ __forceinline__ float face_weight(const int4 *__restrict__ tets, int4 r, int boff, int target)
+{
+    if (r.x < 0) return 0.f;
+    const int j = r.x >> 2, s = r.x & 3;
+    const int4 tv = __ldg(&tets[j]);
+    const int f0 = boff + (s == 0 ? tv.y : tv.x), f1 = boff + (s <= 1 ? tv.z : tv.y),
+              f2 = boff + (s <= 2 ? tv.w : tv.z);
+    return target == f0 ? __int_as_float(r.y)
+           : target == f1 ? __int_as_float(r.z)
+           : target == f2 ? __int_as_float(r.w)
+                          : 0.f;
+}
+
+// cand[c] = the parent p of c (weight > 0) whose own parent face holds c
+// (weight > 0), when there is exactly one such parent; else -1
+__global__ void k_adj_cand(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
+                           int *cand)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tot) return;
+    const int4 r = rec[g];
+    int c = -1, found = 0;
+    if (r.x >= 0) {
+        const int boff = (g / n_v) * n_v;
+        const int j = r.x >> 2, s = r.x & 3;
+        const int4 tv = __ldg(&tets[j]);
+        const int f[3] = {boff + (s == 0 ? tv.y : tv.x), boff + (s <= 1 ? tv.z : tv.y), boff + (s <= 2 ? tv.w : tv.z)};
+        const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            if (al[q] == 0.f) continue;
+            if (face_weight(tets, rec[f[q]], boff, g) != 0.f) {
+                c = f[q];
+                ++found;
+            }
+        }
+    }
+    cand[g] = found == 1 ? c : -1;
+}
+
+// pair[c] = cand[c] when the candidacy is mutual and 1 - a_cp a_pc is not
+// tiny; also clears the pair's hand-over word
+__global__ void k_adj_pair(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
+                           const int *__restrict__ cand, int *pair, unsigned long long *pairw)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= n_tot) return;
+    int p = cand[g];
+    if (p >= 0 && cand[p] == g) {
+        const int boff = (g / n_v) * n_v;
+        const float a_gp = face_weight(tets, rec[g], boff, p), a_pg = face_weight(tets, rec[p], boff, g);
+        if (!(1.f - a_gp * a_pg > 1e-6f)) p = -1;
+    } else {
+        p = -1;
+    }
+    pair[g] = p;
+    pairw[g] = 0ull;
+}
+
 __global__ void k_adj_count(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
-                            unsigned long long *w)
+                            const int *__restrict__ pair, unsigned long long *w)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tot) return;
@@ -194,11 +263,13 @@ __global__ void k_adj_count(int n_v, int n_tot, const int4 *__restrict__ rec, co
     int4 tv = tets[j];
     int ids[4] = {boff + tv.x, boff + tv.y, boff + tv.z, boff + tv.w};
     int al[3] = {r.y, r.z, r.w};
+    const int partner = pair[i];
     int q3 = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         if (q == s) continue;
-        if (__int_as_float(al[q3]) != 0.f) atomicAdd(&w[ids[q]], ADJ_ONE);
+        // the edge to a 2-cycle partner is solved with the pair, not counted
+        if (__int_as_float(al[q3]) != 0.f && ids[q] != partner) atomicAdd(&w[ids[q]], ADJ_ONE);
         ++q3;
     }
 }
@@ -267,7 +338,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     if (tid == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[0]));
     // ---- dataflow phase (no grid barrier per level) ----
     // The vertices readied so far sit in a work queue of (vertex, mu) items
-    // (lists[0..2 n_tot) as n_tot 64-bit slots, empty = all ones); q_res counts
+    // (lists[0..3 n_tot) as qcap = 1.5 n_tot 64-bit slots, empty = all ones:
+    // every vertex is queued at most once, the second member of a 2-cycle at
+    // most twice); q_res counts
     // the slots produced, q_head the slots handed out, and q_active the
     // queued items plus chains in progress (it reaches zero only when no
     // more work can appear).  Each warp runs up to 32 chains in lockstep:
@@ -282,7 +355,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     unsigned long long *queue = reinterpret_cast<unsigned long long *>(a.lists);
     const int lane = threadIdx.x & 31;
     int v = -1;        // vertex this lane is processing
-    float m = 0.f;     // its mu
+    float m = 0.f;     // its mu (or, for a 2-cycle member not yet solved, lambda + the other children's pushes)
+    bool pre = false;  // v is a 2-cycle member whose pair is already solved (m is its mu)
     int pending = -1;  // a slot handed to this lane that was still empty
     unsigned int idle_spins = 0, sleep_ns = 32;
     for (;;) {
@@ -305,11 +379,13 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         // a slot handed out may still be empty if other warps took the items
         // counted as available; it fills once its producer stores it
         if (pending >= 0) {
-            const unsigned long long item = pending < n_tot ? ld_relaxed_u64(&queue[pending]) : 0ull;
-            if (pending >= n_tot) {
-                pending = -1;  // cannot happen: at most n_tot items are ever queued
+            const unsigned long long item = pending < a.qcap ? ld_relaxed_u64(&queue[pending]) : 0ull;
+            if (pending >= a.qcap) {
+                pending = -1;  // cannot happen: at most n_tot + n_tot / 2 items are ever queued
             } else if (item != ~0ull) {
-                v = (int)(unsigned int)(item & 0xffffffffu);
+                const unsigned int vv = (unsigned int)(item & 0xffffffffu);
+                v = (int)(vv & 0x7fffffffu);
+                pre = (vv >> 31) != 0u;
                 m = __uint_as_float((unsigned int)(item >> 32));
                 pending = -1;
             }
@@ -320,11 +396,34 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             const int b = v / (int)n_v;
             const int boff = b * (int)n_v;
             const int4 r = __ldg(&a.rec[v]);
+            const int partner = __ldg(&a.pair[v]);
+            bool go = true;
+            if (partner >= 0 && !pre) {
+                // 2-cycle: the first member to be ready leaves its sum in the
+                // pair's word and stops; the second solves the pair
+                const int slot = min(v, partner);
+                const unsigned long long own = (2ull << 32) | __float_as_uint(m);
+                const unsigned long long old = atomicCAS(&a.pairw[slot], 0ull, own);
+                if (old == 0ull) {
+                    go = false;
+                } else {
+                    const float mq = __uint_as_float((unsigned int)(old & 0xffffffffu));
+                    const float a_vq = face_weight(a.tets, r, boff, partner);              // partner in v's face
+                    const float a_qv = face_weight(a.tets, __ldg(&a.rec[partner]), boff, v);  // v in partner's face
+                    const float mv = (m + a_qv * mq) / (1.f - a_vq * a_qv);
+                    m = mv;
+                    atomicAdd(&a.ctl->q_active, 1);
+                    const int pos = atomicAdd(&a.ctl->q_res, 1);
+                    st_relaxed_u64(&queue[pos], adj_item((int)((unsigned int)partner | 0x80000000u), mq + a_vq * mv));
+                }
+            }
+            pre = false;
+            int next = -1;
+            float mnext = 0.f;
+            if (go) {
             a.mu[v] = m;
             a.proc[v] = 1;
             ++mine;
-            int next = -1;
-            float mnext = 0.f;
             if (r.x >= 0) {
                 const int j = r.x >> 2, s = r.x & 3;
                 const int4 tv = __ldg(&a.tets[j]);
@@ -334,10 +433,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                 unsigned long long nw[3] = {0ull, 0ull, 0ull};
                 float lp[3];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) lp[q] = al[q] != 0.f ? __ldg(&a.lam[f[q]]) : 0.f;
+                for (int q = 0; q < 3; ++q) lp[q] = al[q] != 0.f && f[q] != partner ? __ldg(&a.lam[f[q]]) : 0.f;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    if (al[q] == 0.f) continue;
+                    if (al[q] == 0.f || f[q] == partner) continue;
                     const long long c = __double2ll_rn((double)(al[q] * m) * scale);
                     const unsigned long long d = (unsigned long long)c - ADJ_ONE;
                     nw[q] = atomicAdd(&a.w[f[q]], d) + d;
@@ -345,7 +444,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                 local_terms(a, b, v - boff, r, m);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    if (al[q] == 0.f || adj_count(nw[q]) != 0u) continue;
+                    if (al[q] == 0.f || f[q] == partner || adj_count(nw[q]) != 0u) continue;
                     // this push completed f[q]: its mu is lambda plus the whole sum
                     const float mp = lp[q] + (float)((double)adj_sum(nw[q]) * iscale);
                     if (next < 0) {
@@ -359,6 +458,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                 }
             } else {
                 local_terms(a, b, v - boff, r, m);
+            }
             }
             v = next;
             m = mnext;
@@ -392,7 +492,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                 const unsigned long long item = ld_relaxed_u64(&queue[pending]);
                 pending = -1;
                 if (item != ~0ull) {
-                    v = (int)(unsigned int)(item & 0xffffffffu);
+                    const unsigned int vv = (unsigned int)(item & 0xffffffffu);
+                    v = (int)(vv & 0x7fffffffu);
+                    pre = (vv >> 31) != 0u;
                     m = __uint_as_float((unsigned int)(item >> 32));
                 }
             }
@@ -422,7 +524,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     // ---- vertices blocked by cycles: fixed-point iteration ----
     // collect the unprocessed reached vertices R (closed under parents); the
     // barrier above ordered every write of the dataflow phase before this
-    int *R = a.lists + 2 * n_tot;
+    int *R = a.lists + 3 * n_tot;
     for (int64_t base = 0; base < n_tot; base += nth) {
         const int64_t i = base + tid;
         bool app = i < n_tot && __ldcg(&a.proc[i]) == 0;
@@ -539,7 +641,8 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     err = cudaMemsetAsync(&c->ctl->q_active, 0, sizeof(int), c->stream);
     if (err) return err;
     const int64_t n_tot = n_v * c->nb;
-    err = cudaMemsetAsync(c->lists, 0xff, sizeof(unsigned long long) * n_tot, c->stream);  // empty queue slots
+    const int64_t qcap = (3 * n_tot) / 2;  // 64-bit queue slots in lists[0 .. 3 n_tot)
+    err = cudaMemsetAsync(c->lists, 0xff, sizeof(unsigned long long) * qcap, c->stream);  // empty queue slots
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->adj_levels, 0, offsetof(Control, adj_ts) - offsetof(Control, adj_levels),
                           c->stream);
@@ -552,7 +655,11 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     unsigned bl = (unsigned)((n_tot + th - 1) / th);
     time_begin(c, 4);
     k_adj_init<<<bl, th, 0, c->stream>>>(n_tot, c->rec, dphi, c->adj_w, c->proc, c->ctl);
-    k_adj_count<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_w);
+    k_adj_cand<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_cand);
+    k_adj_pair<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_cand, c->adj_pair,
+                                         c->adj_pairw);
+    k_adj_count<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_pair, c->adj_w);
+    c->launches += 2;
     if (c->max_nbr > ADJ_MAX_CHILDREN) {
         k_adj_check<<<bl, th, 0, c->stream>>>(n_tot, c->adj_w, c->ctl);
         c->launches++;
@@ -575,6 +682,9 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.rec = c->rec;
     a.onset_kind = c->onset_kind;
     a.site_per_problem = c->site_b > 0;
+    a.pair = c->adj_pair;
+    a.pairw = c->adj_pairw;
+    a.qcap = qcap;
     a.on_idx = c->on_idx;
     a.on_bary = c->on_bary;
     a.lam = dphi;

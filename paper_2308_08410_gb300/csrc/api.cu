@@ -79,6 +79,9 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->jac_acc);
     dfree(&c->jac_acc2);
     dfree(&c->adj_w);
+    dfree(&c->adj_cand);
+    dfree(&c->adj_pair);
+    dfree(&c->adj_pairw);
     dfree(&c->proc);
     dfree(&c->L);
     dfree(&c->Lbf);
@@ -381,13 +384,16 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(dalloc(&c->rec, n_v));
     CK(dalloc(&c->chg, n_v));
     CK(dalloc(&c->stamp, n_v));
-    CK(dalloc(&c->lists, 3 * n_v + 32));
+    CK(dalloc(&c->lists, 4 * n_v + 32));
     CK(dalloc(&c->keys, n_v));
     CK(dalloc(&c->mu, n_v));
     CK(dalloc(&c->jac_x, n_v));
     CK(dalloc(&c->jac_acc, n_v));
     CK(dalloc(&c->jac_acc2, n_v));
     CK(dalloc(&c->adj_w, n_v));
+    CK(dalloc(&c->adj_cand, n_v));
+    CK(dalloc(&c->adj_pair, n_v));
+    CK(dalloc(&c->adj_pairw, n_v));
     CK(dalloc(&c->proc, n_v));
     CK(dalloc(&c->dphi, n_v));
     CK(cudaMemset(c->dphi, 0, sizeof(float) * n_v));
@@ -810,13 +816,16 @@ static cudaError_t ensure_batch(gbp_ctx *c, int B)
     CK(dalloc(&c->rec, nv));
     CK(dalloc(&c->chg, nv));
     CK(dalloc(&c->stamp, nv));
-    CK(dalloc(&c->lists, 3 * nv + 32));
+    CK(dalloc(&c->lists, 4 * nv + 32));
     CK(dalloc(&c->keys, nv));
     CK(dalloc(&c->mu, nv));
     CK(dalloc(&c->jac_x, nv));
     CK(dalloc(&c->jac_acc, nv));
     CK(dalloc(&c->jac_acc2, nv));
     CK(dalloc(&c->adj_w, nv));
+    CK(dalloc(&c->adj_cand, nv));
+    CK(dalloc(&c->adj_pair, nv));
+    CK(dalloc(&c->adj_pairw, nv));
     CK(dalloc(&c->proc, nv));
     CK(dalloc(&c->dphi, nv));
     CK(dalloc(&c->pc, nv));

@@ -71,6 +71,8 @@ struct gbp_ctx {
     // adjoint state
     float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;
     unsigned long long *adj_w = nullptr;  // adjoint: packed (child count, push sum) per vertex
+    int *adj_cand = nullptr, *adj_pair = nullptr;  // adjoint: 2-cycle candidates and partners per vertex
+    unsigned long long *adj_pairw = nullptr;       // adjoint: hand-over word of each 2-cycle (at its smaller entry)
     int *proc = nullptr;
     int max_nbr = 0;  // longest vertex->vertex row (bounds a vertex's child count)
     // ECG scratch
