@@ -50,7 +50,6 @@ struct AdjArgs {
     const float4 *xyz;
     const int4 *tets;
     const float4 *tf;  // unit fibre per tet (shared by the batch)
-    const float *tsd;
     const float *cf, *ct;
     const int4 *rec;
     int onset_kind;
@@ -676,7 +675,6 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.xyz = c->xyz;
     a.tets = c->tets;
     a.tf = c->tf;
-    a.tsd = c->tsd;
     a.cf = c->cf;
     a.ct = c->ct;
     a.rec = c->rec;

@@ -63,8 +63,6 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->fib);
     dfree(&c->cf);
     dfree(&c->ct);
-    dfree(&c->tm);
-    dfree(&c->tsd);
     dfree(&c->tf);
     dfree(&c->tv);
     dfree(&c->tlip);
@@ -375,8 +373,6 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(dalloc(&c->fib, 3 * n_t));
     CK(dalloc(&c->cf, n_t));
     CK(dalloc(&c->ct, n_t));
-    CK(dalloc(&c->tm, n_t));
-    CK(dalloc(&c->tsd, n_t));
     CK(dalloc(&c->tf, n_t));
     CK(dalloc(&c->tv, n_t));
     CK(dalloc(&c->tlip, n_t));
@@ -808,8 +804,6 @@ static cudaError_t ensure_batch(gbp_ctx *c, int B)
     CK(cudaStreamSynchronize(c->stream));
     CK(dalloc(&c->cf, nt));
     CK(dalloc(&c->ct, nt));
-    CK(dalloc(&c->tm, nt));
-    CK(dalloc(&c->tsd, nt));
     CK(dalloc(&c->tv, nt));
     CK(dalloc(&c->tlip, nt));
     CK(dalloc(&c->phi, nv));

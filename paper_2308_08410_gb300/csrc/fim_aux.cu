@@ -9,10 +9,13 @@ namespace gbp {
 // ---------------------------------------------------------------------------
 // per-tet metric (Sec. II-A): R = D^{1/2} in factored form
 // ---------------------------------------------------------------------------
-// Batched: entry g = b * n_t + j of the per-problem arrays (cf, ct, tm, tsd).
+// Batched: entry g = b * n_t + j of the per-problem arrays (cf, ct, tv).
+// The metric of tet j in problem b is kept as the unit fibre tf[j] (shared by
+// the batch) and tv[g] = (1/ct, 1/cf - 1/ct): R = D^{1/2} applied to e is
+// e / ct + (1/cf - 1/ct) (f.e) f.
 __global__ void k_precompute(int64_t n_t, int64_t n_tot, const float *__restrict__ fib, const float *__restrict__ cf,
-                             const float *__restrict__ ct, float4 *__restrict__ tm, float *__restrict__ tsd,
-                             float4 *__restrict__ tf, float2 *__restrict__ tv, Control *ctl)
+                             const float *__restrict__ ct, float4 *__restrict__ tf, float2 *__restrict__ tv,
+                             Control *ctl)
 {
     int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= n_tot) return;
@@ -28,10 +31,6 @@ __global__ void k_precompute(int64_t n_t, int64_t n_tot, const float *__restrict
     }
     float in = 1.f / nn;
     float sa = 1.f / vt;
-    tm[g] = make_float4(fx * in, fy * in, fz * in, sa);
-    tsd[g] = 1.f / vf - sa;
-    // the FIM's compact copy: the fibre once per tet (shared by the batch),
-    // the two velocity terms per problem
     tv[g] = make_float2(sa, 1.f / vf - sa);
     if (g < n_t) tf[g] = make_float4(fx * in, fy * in, fz * in, 0.f);
 }
@@ -41,20 +40,22 @@ cudaError_t launch_precompute(gbp_ctx *c)
     int th = 256;
     const int64_t n_tot = c->n_t * c->nb;
     int64_t bl = (n_tot + th - 1) / th;
-    k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->fib, c->cf, c->ct, c->tm, c->tsd, c->tf, c->tv,
+    k_precompute<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->fib, c->cf, c->ct, c->tf, c->tv,
                                                      c->ctl);
     c->launches++;
     return cudaGetLastError();
 }
 
 __global__ void k_lipschitz(int64_t n_t, int64_t n_tot, const float4 *__restrict__ xyz, const int4 *__restrict__ tets,
-                            const float4 *__restrict__ tm, const float *__restrict__ tsd, float4 *__restrict__ tlip)
+                            const float4 *__restrict__ tf, const float2 *__restrict__ tvel, float4 *__restrict__ tlip)
 {
     int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (g >= n_tot) return;
     int4 tv = tets[g % n_t];
-    float4 m = tm[g];
-    float sd = tsd[g];
+    const float4 f = tf[g % n_t];
+    const float2 v2 = tvel[g];
+    const float4 m = make_float4(f.x, f.y, f.z, v2.x);
+    const float sd = v2.y;
     float L[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -71,7 +72,7 @@ cudaError_t launch_lipschitz(gbp_ctx *c)
     int th = 256;
     const int64_t n_tot = c->n_t * c->nb;
     int64_t bl = (n_tot + th - 1) / th;
-    k_lipschitz<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->xyz, c->tets, c->tm, c->tsd, c->tlip);
+    k_lipschitz<<<(unsigned)bl, th, 0, c->stream>>>(c->n_t, n_tot, c->xyz, c->tets, c->tf, c->tv, c->tlip);
     c->launches++;
     return cudaGetLastError();
 }
@@ -87,8 +88,8 @@ __global__ void k_onset_keys(int K, int nb, int per_problem, int kind, const int
                              const float *__restrict__ bary,
                              const float *__restrict__ t, int64_t n_v, int64_t n_real, int64_t n_t,
                              const float4 *__restrict__ xyz,
-                             const int4 *__restrict__ tets, const float4 *__restrict__ tm,
-                             const float *__restrict__ tsd, unsigned long long *keys_all, Control *ctl)
+                             const int4 *__restrict__ tets, const float4 *__restrict__ tf,
+                             const float2 *__restrict__ tvel, unsigned long long *keys_all, Control *ctl)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= K * nb) return;
@@ -121,8 +122,10 @@ __global__ void k_onset_keys(int K, int nb, int per_problem, int kind, const int
             xo.y = fmaf(b, x[q].y, xo.y);
             xo.z = fmaf(b, x[q].z, xo.z);
         }
-        float4 m = tm[(int64_t)b * n_t + id];
-        float sd = tsd[(int64_t)b * n_t + id];
+        const float4 fe = tf[id];
+        const float2 ve = tvel[(int64_t)b * n_t + id];
+        const float4 m = make_float4(fe.x, fe.y, fe.z, ve.x);
+        const float sd = ve.y;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             float3 w = xform(make_float3(x[q].x - xo.x, x[q].y - xo.y, x[q].z - xo.z), m, sd);
@@ -197,7 +200,7 @@ cudaError_t launch_fim_seed(gbp_ctx *c)
     k_onset_keys<<<(c->K * c->nb + th - 1) / th, th, 0, c->stream>>>(c->K, c->nb, c->site_b > 0,
                                                                       c->onset_kind, c->on_idx, c->on_bary,
                                                                       c->on_t, n_v, c->n_e, c->n_t, c->xyz,
-                                                                      c->tets, c->tm, c->tsd, c->keys, c->ctl);
+                                                                      c->tets, c->tf, c->tv, c->keys, c->ctl);
     const unsigned bl = (unsigned)((n_tot + th - 1) / th);
     k_init_nodes<<<bl, th, 0, c->stream>>>(n_tot, c->keys, c->phi, c->rec, c->chg, c->stamp, c->pc);
     k_seed_lists<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->keys, c->n2n_ptr, c->n2n, c->stamp,
@@ -224,8 +227,8 @@ cudaError_t launch_unpack_state(gbp_ctx *c)
 // weights of the triangle's two other vertices (the apex weight is 0).
 template <int MODE>
 __global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t, const float4 *__restrict__ xyz,
-                              const int4 *__restrict__ tets, const float4 *__restrict__ tm_all,
-                              const float *__restrict__ tsd_all, const float4 *__restrict__ tlip_all, int n_f,
+                              const int4 *__restrict__ tets, const float4 *__restrict__ tf,
+                              const float2 *__restrict__ tv_all, const float4 *__restrict__ tlip_all, int n_f,
                               const float *__restrict__ phi_all, int4 *rec, float *out_phi, int32_t *out_parent,
                               float *out_alpha, Control *ctl)
 {
@@ -233,8 +236,7 @@ __global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t,
     if (g >= n_tot) return;
     const int b = g / n_v;
     const float *phi = phi_all + (int64_t)b * n_v;
-    const float4 *tm = tm_all + (int64_t)b * n_t;
-    const float *tsd = tsd_all + (int64_t)b * n_t;
+    const float2 *tvb = tv_all + (int64_t)b * n_t;
     const float4 *tlip = tlip_all + (int64_t)b * n_t;
     const int i = g;
     int4 r = rec[i];
@@ -246,7 +248,9 @@ __global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t,
         int4 tv = tets[j];
         float3 p[3];
         int fv[3];
-        face_vectors(xyz, tv, s, tm[j], tsd[j], p, fv);
+        const float4 fj = tf[j];
+        const float2 vj = tvb[j];
+        face_vectors(xyz, tv, s, make_float4(fj.x, fj.y, fj.z, vj.x), vj.y, p, fv);
         float ph[3] = {phi[fv[0]], phi[fv[1]], phi[fv[2]]};
         LocalRes lr;
         int fb = 0;
@@ -289,11 +293,11 @@ cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_
     time_begin(c, 1);
     if (mode == GBP_LOCAL_FISTA)
         k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
-                                                                 c->xyz, c->tets, c->tm, c->tsd, c->tlip, n_f,
+                                                                 c->xyz, c->tets, c->tf, c->tv, c->tlip, n_f,
                                                                  c->phi, c->rec, phi, parent, alpha, c->ctl);
     else
         k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
-                                                                 c->xyz, c->tets, c->tm, c->tsd, c->tlip, n_f,
+                                                                 c->xyz, c->tets, c->tf, c->tv, c->tlip, n_f,
                                                                  c->phi, c->rec, phi, parent, alpha, c->ctl);
     time_end(c, 1);
     c->launches++;

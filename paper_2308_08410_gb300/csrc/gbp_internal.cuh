@@ -37,8 +37,6 @@ struct gbp_ctx {
     int *n2n_ptr = nullptr, *n2n = nullptr;
     int4 *frec = nullptr;  // per vertex->tet entry: face vertex ids (slot order), tet*4 + slot
     float *fib = nullptr, *cf = nullptr, *ct = nullptr;
-    float4 *tm = nullptr;   // (fx, fy, fz, 1/ct)
-    float *tsd = nullptr;   // 1/cf - 1/ct
     float4 *tf = nullptr;   // unit fibre per tet (shared by the problems of a batch)
     float2 *tv = nullptr;   // (1/ct, 1/cf - 1/ct) per tet and problem
     float4 *tlip = nullptr; // FISTA Lipschitz constants per (tet, slot)
