@@ -898,12 +898,14 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opt
     }
     if (!e) e = gbp::launch_fim(c, &o);
     if (!e) e = gbp::launch_parent_pass(c, o.local_solver, o.n_f, nullptr, nullptr, nullptr);
-    for (int b = 0; b < B && !e; ++b) {
-        e = gbp::launch_ecg_forward(c, c->phi + b * n_v, tmpl, precision, V + b * NT);
-        if (!e)
-            e = gbp::launch_ecg_backward(c, c->phi + b * n_v, V + b * NT, target + b * NT, tmpl, loss + b,
-                                         c->dphi + b * n_v);
+    // the ECG and misfit of all B problems in one launch each (the BF16
+    // forward still runs problem by problem)
+    if (precision == GBP_PREC_BF16) {
+        for (int b = 0; b < B && !e; ++b) e = gbp::launch_ecg_forward(c, c->phi + b * n_v, tmpl, precision, V + b * NT);
+    } else if (!e) {
+        e = gbp::launch_ecg_forward_fp32_batch(c, B, c->phi, n_v, tmpl, V);
     }
+    if (!e) e = gbp::launch_ecg_backward_batch(c, B, c->phi, n_v, V, target, tmpl, loss, c->dphi);
     if (!e) e = run_adjoint(c, c->dphi, d_cf, d_ct, d_t, d_x);
     // the context's single-problem state is gone: the next single-problem
     // evaluation starts from gbp_set_velocities

@@ -30,11 +30,16 @@ __device__ __forceinline__ float logistic(float z) { return 1.f / (1.f + expf(-z
 // sums in FP64: the terms of one lead can cancel by orders of magnitude
 // (its lead-field row sums to zero), and a long FP32 running sum would
 // carry its rounding times that cancellation into the result.
+// Problem blockIdx.y of a batch reads phi + blockIdx.y * phi_stride and
+// writes part + blockIdx.y * part_stride.
 template <int NL>
 __global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const float *__restrict__ L,
                                                    const float *__restrict__ phi, float t0, float dt, float c4,
-                                                   int T_tile, int G, int64_t per_cta, double *__restrict__ part)
+                                                   int T_tile, int G, int64_t per_cta, double *__restrict__ part,
+                                                   int64_t phi_stride, int64_t part_stride)
 {
+    phi += blockIdx.y * phi_stride;
+    part += blockIdx.y * part_stride;
     extern __shared__ double smd[];
     double *red = smd;                                        // [G][NL][T_tile]
     float *sphi = reinterpret_cast<float *>(red + (size_t)G * NL * T_tile);  // [ECG_CH]
@@ -88,29 +93,41 @@ __global__ void __launch_bounds__(512) k_ecg_fwd_t(int64_t n_v, int T, const flo
 }
 
 template <int NL>
-static cudaError_t launch_fwd_n(int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
+static cudaError_t launch_fwd_n(int ncta, int nb, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
-                                int64_t per, double *part)
+                                int64_t per, double *part, int64_t phi_stride, int64_t part_stride)
 {
     cudaFuncSetAttribute(k_ecg_fwd_t<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ecg_fwd_t<NL><<<ncta, threads, smem, st>>>(n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part);
+    k_ecg_fwd_t<NL><<<dim3(ncta, nb), threads, smem, st>>>(n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part,
+                                                           phi_stride, part_stride);
     return cudaGetLastError();
 }
 
-// one instantiation per lead count 1..16
-cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
-                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
-                                 int64_t per, double *part)
+// one instantiation per lead count 1..16; nb problems (grid y)
+static cudaError_t launch_ecg_fwd_leads_b(int N, int ncta, int nb, int threads, size_t smem, cudaStream_t st,
+                                          int64_t n_v, int T, const float *L, const float *phi, float t0, float dt,
+                                          float c4, int T_tile, int G, int64_t per, double *part, int64_t phi_stride,
+                                          int64_t part_stride)
 {
     switch (N) {
 #define GBP_ECG_CASE(n) \
-    case n: return launch_fwd_n<n>(ncta, threads, smem, st, n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part);
+    case n: return launch_fwd_n<n>(ncta, nb, threads, smem, st, n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part, \
+                                   phi_stride, part_stride);
         GBP_ECG_CASE(1) GBP_ECG_CASE(2) GBP_ECG_CASE(3) GBP_ECG_CASE(4) GBP_ECG_CASE(5) GBP_ECG_CASE(6)
         GBP_ECG_CASE(7) GBP_ECG_CASE(8) GBP_ECG_CASE(9) GBP_ECG_CASE(10) GBP_ECG_CASE(11) GBP_ECG_CASE(12)
         GBP_ECG_CASE(13) GBP_ECG_CASE(14) GBP_ECG_CASE(15) GBP_ECG_CASE(16)
 #undef GBP_ECG_CASE
     }
     return cudaErrorInvalidValue;
+}
+
+// one problem (also used by the allocation-free entry point)
+cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
+                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
+                                 int64_t per, double *part)
+{
+    return launch_ecg_fwd_leads_b(N, ncta, 1, threads, smem, st, n_v, T, L, phi, t0, dt, c4, T_tile, G, per, part, 0,
+                                  0);
 }
 
 // V[l][s] = K0 S_l + (K1 - K0) sum_cta part[cta][l][s]  (fixed order, FP64)
@@ -122,6 +139,22 @@ __global__ void k_ecg_reduce(int N, int T, int ncta, const double *__restrict__ 
     int l = e / T;
     double v = 0.0;
     for (int c = 0; c < ncta; ++c) v += part[(int64_t)c * N * T + e];
+    ecg[e] = (float)((double)K0 * rowsum[l] + (double)dK * v);
+}
+
+// the same for nb problems: entry e of [nb][N][T], partials of problem b at
+// part + b * part_stride
+__global__ void k_ecg_reduce_b(int N, int T, int nb, int ncta, const double *__restrict__ part, int64_t part_stride,
+                               const float *__restrict__ rowsum, float K0, float dK, float *__restrict__ ecg)
+{
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int NT = N * T;
+    if (e >= (int64_t)nb * NT) return;
+    const int b = (int)(e / NT), en = (int)(e - (int64_t)b * NT);
+    const int l = en / T;
+    const double *pb = part + b * part_stride;
+    double v = 0.0;
+    for (int c = 0; c < ncta; ++c) v += pb[(int64_t)c * NT + en];
     ecg[e] = (float)((double)K0 * rowsum[l] + (double)dK * v);
 }
 
@@ -142,7 +175,9 @@ static void ecg_fwd_shape(int T, int *T_tile, int *G)
     *G = g;
 }
 
-cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_template *t, float *ecg)
+// nb problems: phi [b] at phi + b * phi_stride, ecg [nb][N][T]
+cudaError_t launch_ecg_forward_fp32_batch(gbp_ctx *c, int nb, const float *phi, int64_t phi_stride,
+                                          const gbp_template *t, float *ecg)
 {
     const int N = c->N, T = t->T;
     int T_tile, G;
@@ -151,7 +186,8 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
     int64_t per = (c->n_e + ncta - 1) / ncta;
     per = ((per + ECG_CH - 1) / ECG_CH) * ECG_CH;
     ncta = (int)((c->n_e + per - 1) / per);
-    int64_t need = 2 * (int64_t)ncta * N * T;  // FP64 partials, counted in floats
+    const int64_t part_stride = (int64_t)ncta * N * T;  // doubles per problem
+    int64_t need = 2 * part_stride * nb;                // FP64 partials, counted in floats
     if (need > c->ecg_part_cap) {
         if (c->ecg_part) cudaFree(c->ecg_part);
         cudaError_t err = cudaMalloc(&c->ecg_part, sizeof(float) * need);
@@ -166,23 +202,34 @@ cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_temp
     size_t smem = ecg_fwd_smem(N, T_tile, G);
     float c4 = 4.f / t->tau;
     time_begin(c, 2);
-    cudaError_t le = launch_ecg_fwd_leads(N, ncta, T_tile * G, smem, c->stream, c->n_e, T, c->L, phi, t->t0, t->dt,
-                                          c4, T_tile, G, per, part);
+    cudaError_t le = launch_ecg_fwd_leads_b(N, ncta, nb, T_tile * G, smem, c->stream, c->n_e, T, c->L, phi, t->t0,
+                                            t->dt, c4, T_tile, G, per, part, phi_stride, part_stride);
     if (le) return le;
-    k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, c->stream>>>(N, T, ncta, part, c->Lrowsum, t->K0, t->K1 - t->K0,
-                                                            ecg);
+    const int64_t tot = (int64_t)nb * N * T;
+    k_ecg_reduce_b<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(N, T, nb, ncta, part, part_stride,
+                                                                         c->Lrowsum, t->K0, t->K1 - t->K0, ecg);
     time_end(c, 2);
     c->launches += 2;
     return cudaGetLastError();
+}
+
+cudaError_t launch_ecg_forward_fp32(gbp_ctx *c, const float *phi, const gbp_template *t, float *ecg)
+{
+    return launch_ecg_forward_fp32_batch(c, 1, phi, 0, t, ecg);
 }
 
 // ---------------------------------------------------------------------------
 // misfit and its derivative in phi
 // ---------------------------------------------------------------------------
 // r = ecg - target; loss = 1/(N T) sum r^2 (Eq. inverse_ecg, rectangle rule).
+// One block per problem: block b reads [b][N][T] and writes loss[b].
 __global__ void k_ecg_resid(int NT, const float *__restrict__ ecg, const float *__restrict__ target,
                             float *__restrict__ r, float inv_nt, float *__restrict__ loss)
 {
+    ecg += (int64_t)blockIdx.x * NT;
+    target += (int64_t)blockIdx.x * NT;
+    r += (int64_t)blockIdx.x * NT;
+    loss += blockIdx.x;
     __shared__ double red[32];
     double acc = 0.0;
     for (int e = threadIdx.x; e < NT; e += blockDim.x) {
@@ -205,12 +252,17 @@ __global__ void k_ecg_resid(int NT, const float *__restrict__ ecg, const float *
 // 2e-35 and are skipped (their terms vanish against the FP32 sum).  The
 // residual is stored sample-major in shared memory (rT[s][l]) so one sample's
 // leads are contiguous.  NL = number of leads (compile time).
+// Problem blockIdx.y of a batch: phi and dphi at + blockIdx.y * phi_stride,
+// r at + blockIdx.y * NL * T.
 template <int NL>
 __global__ void __launch_bounds__(256) k_ecg_bwd_t(int64_t n_v, int T, const float *__restrict__ L,
                                                    const float *__restrict__ phi, const float *__restrict__ r,
                                                    float t0, float dt, float tau, float scale,
-                                                   float *__restrict__ dphi)
+                                                   float *__restrict__ dphi, int64_t phi_stride)
 {
+    phi += blockIdx.y * phi_stride;
+    dphi += blockIdx.y * phi_stride;
+    r += (int64_t)blockIdx.y * NL * T;
     extern __shared__ float rT[];  // [T][NL]
     for (int e = threadIdx.x; e < NL * T; e += blockDim.x) {
         const int l = e / T, s = e - l * T;
@@ -247,32 +299,33 @@ __global__ void __launch_bounds__(256) k_ecg_bwd_t(int64_t n_v, int T, const flo
 }
 
 template <int NL>
-static cudaError_t launch_bwd_n(unsigned blocks, size_t smem, cudaStream_t st, int64_t n_v, int T, const float *L,
-                                const float *phi, const float *r, float t0, float dt, float tau, float scale,
-                                float *dphi)
+static cudaError_t launch_bwd_n(unsigned blocks, int nb, size_t smem, cudaStream_t st, int64_t n_v, int T,
+                                const float *L, const float *phi, const float *r, float t0, float dt, float tau,
+                                float scale, float *dphi, int64_t phi_stride)
 {
     cudaFuncSetAttribute(k_ecg_bwd_t<NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_ecg_bwd_t<NL><<<blocks, 256, smem, st>>>(n_v, T, L, phi, r, t0, dt, tau, scale, dphi);
+    k_ecg_bwd_t<NL><<<dim3(blocks, nb), 256, smem, st>>>(n_v, T, L, phi, r, t0, dt, tau, scale, dphi, phi_stride);
     return cudaGetLastError();
 }
 
-cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, const float *target,
-                                const gbp_template *t, float *loss, float *dphi)
+// nb problems: phi, dphi [b] at + b * phi_stride; ecg, target [nb][N][T]; loss [nb]
+cudaError_t launch_ecg_backward_batch(gbp_ctx *c, int nb, const float *phi, int64_t phi_stride, const float *ecg,
+                                      const float *target, const gbp_template *t, float *loss, float *dphi)
 {
     const int N = c->N, T = t->T;
     int64_t NT = (int64_t)N * T;
-    if (NT > c->resid_cap) {
+    if (NT * nb > c->resid_cap) {
         if (c->resid) cudaFree(c->resid);
-        cudaError_t err = cudaMalloc(&c->resid, sizeof(float) * NT);
+        cudaError_t err = cudaMalloc(&c->resid, sizeof(float) * NT * nb);
         if (err) {
             c->resid = nullptr;
             c->resid_cap = 0;
             return err;
         }
-        c->resid_cap = NT;
+        c->resid_cap = NT * nb;
     }
     time_begin(c, 3);
-    k_ecg_resid<<<1, 1024, 0, c->stream>>>((int)NT, ecg, target, c->resid, 1.f / (float)NT, loss);
+    k_ecg_resid<<<nb, 1024, 0, c->stream>>>((int)NT, ecg, target, c->resid, 1.f / (float)NT, loss);
     size_t smem = sizeof(float) * NT;  // N * T <= 16 * 4096 floats = 256 KB at most
     if (smem > 200 * 1024) return cudaErrorInvalidValue;
     float scale = -2.f / (float)NT * (t->K1 - t->K0) * (4.f / t->tau);
@@ -280,8 +333,8 @@ cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, 
     cudaError_t le = cudaErrorInvalidValue;
     switch (N) {
 #define GBP_BWD_CASE(n) \
-    case n: le = launch_bwd_n<n>(blocks, smem, c->stream, c->n_e, T, c->L, phi, c->resid, t->t0, t->dt, t->tau, \
-                                 scale, dphi); break;
+    case n: le = launch_bwd_n<n>(blocks, nb, smem, c->stream, c->n_e, T, c->L, phi, c->resid, t->t0, t->dt, \
+                                 t->tau, scale, dphi, phi_stride); break;
         GBP_BWD_CASE(1) GBP_BWD_CASE(2) GBP_BWD_CASE(3) GBP_BWD_CASE(4) GBP_BWD_CASE(5) GBP_BWD_CASE(6)
         GBP_BWD_CASE(7) GBP_BWD_CASE(8) GBP_BWD_CASE(9) GBP_BWD_CASE(10) GBP_BWD_CASE(11) GBP_BWD_CASE(12)
         GBP_BWD_CASE(13) GBP_BWD_CASE(14) GBP_BWD_CASE(15) GBP_BWD_CASE(16)
@@ -291,6 +344,12 @@ cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, 
     time_end(c, 3);
     c->launches += 2;
     return cudaGetLastError();
+}
+
+cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, const float *target,
+                                const gbp_template *t, float *loss, float *dphi)
+{
+    return launch_ecg_backward_batch(c, 1, phi, 0, ecg, target, t, loss, dphi);
 }
 
 // dispatcher (the BF16 tensor-core path lives in ecg_bf16.cu)

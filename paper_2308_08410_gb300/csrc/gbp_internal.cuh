@@ -112,6 +112,10 @@ cudaError_t launch_fim_seed(gbp_ctx *c);     // fim_aux.cu: onset values, state 
 cudaError_t launch_unpack_state(gbp_ctx *c);  // fim_aux.cu: final values from the packed state
 cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_t *parent, float *alpha);
 cudaError_t launch_ecg_forward(gbp_ctx *c, const float *phi, const gbp_template *t, int prec, float *ecg);
+cudaError_t launch_ecg_forward_fp32_batch(gbp_ctx *c, int nb, const float *phi, int64_t phi_stride,
+                                          const gbp_template *t, float *ecg);
+cudaError_t launch_ecg_backward_batch(gbp_ctx *c, int nb, const float *phi, int64_t phi_stride, const float *ecg,
+                                      const float *target, const gbp_template *t, float *loss, float *dphi);
 cudaError_t launch_ecg_backward(gbp_ctx *c, const float *phi, const float *ecg, const float *target,
                                 const gbp_template *t, float *loss, float *dphi);
 cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_ct, float *d_t, float *d_x);
