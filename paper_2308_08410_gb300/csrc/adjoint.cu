@@ -389,8 +389,11 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                 pending = -1;
             }
         }
-        // one vertex per busy lane (entry v = b * n_v + vertex)
+        // one vertex per busy lane (entry v = b * n_v + vertex); the items it
+        // queues are reserved for the whole warp at once below
         int ended = 0;
+        unsigned long long pend[3];
+        int npend = 0;
         if (v >= 0) {
             const int b = v / (int)n_v;
             const int boff = b * (int)n_v;
@@ -411,9 +414,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                     const float a_qv = face_weight(a.tets, __ldg(&a.rec[partner]), boff, v);  // v in partner's face
                     const float mv = (m + a_qv * mq) / (1.f - a_vq * a_qv);
                     m = mv;
-                    atomicAdd(&a.ctl->q_active, 1);
-                    const int pos = atomicAdd(&a.ctl->q_res, 1);
-                    st_relaxed_u64(&queue[pos], adj_item((int)((unsigned int)partner | 0x80000000u), mq + a_vq * mv));
+                    pend[npend++] = adj_item((int)((unsigned int)partner | 0x80000000u), mq + a_vq * mv);
                 }
             }
             pre = false;
@@ -450,9 +451,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                         next = f[q];
                         mnext = mp;
                     } else {
-                        atomicAdd(&a.ctl->q_active, 1);
-                        const int pos = atomicAdd(&a.ctl->q_res, 1);
-                        st_relaxed_u64(&queue[pos], adj_item(f[q], mp));
+                        pend[npend++] = adj_item(f[q], mp);
                     }
                 }
             } else {
@@ -462,6 +461,25 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             v = next;
             m = mnext;
             ended = v < 0;
+        }
+        // queue this pass's extra items: one reservation for the warp (the
+        // count of live work rises before any chain of the warp retires)
+        const int wsum = __reduce_add_sync(0xffffffffu, npend);
+        if (wsum) {
+            int base = 0;
+            if (lane == 0) {
+                atomicAdd(&a.ctl->q_active, wsum);
+                base = atomicAdd(&a.ctl->q_res, wsum);
+            }
+            base = __shfl_sync(0xffffffffu, base, 0);
+            int incl = npend;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            const int pos = base + incl - npend;
+            for (int k = 0; k < npend; ++k) st_relaxed_u64(&queue[pos + k], pend[k]);
         }
         // retire the chains that ended: their pushes are counted first
         const unsigned int ends = __ballot_sync(0xffffffffu, ended);
