@@ -54,6 +54,7 @@ struct AdjArgs {
     const int4 *rec;
     int onset_kind;
     int site_per_problem;  // on_idx / on_bary hold one site set per problem
+    BarGroup *grp;         // group words of the two-level grid barrier
     const int *pair;       // 2-cycle partner entry of each vertex entry, or -1
     unsigned long long *pairw;  // hand-over word of each 2-cycle, at its smaller entry
     int64_t qcap;          // 64-bit slots of the work queue
@@ -314,11 +315,6 @@ __device__ __forceinline__ int ld_acquire_i32(const int *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release_i32(int *p, int v)
-{
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 #ifndef GBP_ADJ_REFILL
 #define GBP_ADJ_REFILL 8  // idle lanes that make a warp take new items while others are busy
 #endif
@@ -533,7 +529,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     __syncthreads();
     if (threadIdx.x == 0 && s_proc) atomicAdd(&a.ctl->adj_processed, s_proc);
     ++nbar;
-    if (!grid_barrier(a.ctl, nbar) || !ok) return;
+    if (!grid_barrier(a.ctl, a.grp, nbar) || !ok) return;
     if (tid == 0) {
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(a.ctl->adj_ts[1]));
         a.ctl->adj_ts[2] = a.ctl->adj_ts[1];
@@ -556,7 +552,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         warp_append(app, (int)i, R, &a.ctl->count[3]);
     }
     ++nbar;
-    if (!grid_barrier(a.ctl, nbar)) return;
+    if (!grid_barrier(a.ctl, a.grp, nbar)) return;
     const int nR = ld_relaxed_i32(&a.ctl->count[3]);
     if (nR == 0) return;
     // x <- base + P_R^T x with base = mu (lam plus the pushes of processed
@@ -584,7 +580,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         push(i, ld_cg_f(&a.xj[i]), acc_cur);
     }
     ++nbar;
-    if (!grid_barrier(a.ctl, nbar)) return;
+    if (!grid_barrier(a.ctl, a.grp, nbar)) return;
     int it = 0;
     for (; it < a.max_cycle_iters; ++it) {
         // slot (it+1)%3 was last read before the previous barrier
@@ -613,7 +609,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             if (xmax > 0.f) atomicMax((int *)&a.ctl->adj_xmax[it % 3], __float_as_int(xmax));
         }
         ++nbar;
-        if (!grid_barrier(a.ctl, nbar)) return;
+        if (!grid_barrier(a.ctl, a.grp, nbar)) return;
         const float gd = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_delta[it % 3]));
         const float gx = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_xmax[it % 3]));
         float *t = acc_cur;
@@ -649,7 +645,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->barrier, 0, sizeof(unsigned int) * 2, c->stream);  // arrivals, abort
     if (err) return err;
-    err = cudaMemsetAsync(&c->ctl->bar_gen, 0, sizeof(unsigned int), c->stream);
+    err = cudaMemsetAsync(c->bar_grp, 0, sizeof(BarGroup) * GBP_BAR_GROUPS, c->stream);
     if (err) return err;
     err = cudaMemsetAsync(&c->ctl->q_head, 0, sizeof(int), c->stream);
     if (err) return err;
@@ -698,6 +694,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.rec = c->rec;
     a.onset_kind = c->onset_kind;
     a.site_per_problem = c->site_b > 0;
+    a.grp = c->bar_grp;
     a.pair = c->adj_pair;
     a.pairw = c->adj_pairw;
     a.qcap = qcap;

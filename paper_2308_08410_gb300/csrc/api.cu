@@ -218,6 +218,7 @@ gbp_status gbp_create(gbp_ctx **out, int device, void *stream)
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
     cudaError_t e = cudaMalloc(&c->ctl, sizeof(Control));
     if (!e) e = cudaMemset(c->ctl, 0, sizeof(Control));
+    if (!e) e = cudaMalloc(&c->bar_grp, sizeof(gbp::BarGroup) * gbp::GBP_BAR_GROUPS);
     if (!e) e = cudaMallocHost(&c->h_ctl, sizeof(Control));
     for (int i = 0; i < 64 && !e; ++i) e = cudaEventCreate(&c->ev_pool[i]);
     if (e || !coop) {
@@ -235,6 +236,7 @@ void gbp_destroy(gbp_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_mesh_buffers(c);
     dfree(&c->ctl);
+    dfree(&c->bar_grp);
     dfree(&c->ecg_part);
     dfree(&c->resid);
     dfree(&c->ecg_tmp);

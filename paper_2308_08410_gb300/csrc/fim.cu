@@ -28,6 +28,7 @@ struct FimArgs {
     int4 *rec;
     int *chg, *stamp, *lists;
     Control *ctl;
+    BarGroup *grp;
     float eps;
     int max_iters;
     int n_f;
@@ -253,7 +254,7 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
         __syncthreads();
         for (int q = threadIdx.x; q < s_cnt; q += blockDim.x) nlist[s_base + q] = s_list[q];
         ++nbar;
-        if (!grid_barrier(a.ctl, nbar)) break;
+        if (!grid_barrier(a.ctl, a.grp, nbar)) break;
     }
     // statistics
     unsigned int wf = my_faces;
@@ -328,10 +329,13 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     a.stamp = c->stamp;
     a.lists = c->lists;
     a.ctl = c->ctl;
+    a.grp = c->bar_grp;
     a.eps = o->eps;
     a.max_iters = o->max_iters;
     a.n_f = o->n_f;
     a.trace = trace;
+    err = cudaMemsetAsync(c->bar_grp, 0, sizeof(BarGroup) * GBP_BAR_GROUPS, c->stream);
+    if (err) return err;
     const void *fn = o->local_solver == GBP_LOCAL_FISTA ? (const void *)k_fim<GBP_LOCAL_FISTA>
                                                         : (const void *)k_fim<GBP_LOCAL_EXACT>;
     int grid = fim_grid(c, fn);

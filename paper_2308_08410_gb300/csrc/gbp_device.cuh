@@ -18,13 +18,10 @@ namespace gbp {
 // device control block (one per context)
 // ---------------------------------------------------------------------------
 struct Control {
-    // cache line 0: grid-barrier arrivals (atomics) and the abort flag
-    unsigned int barrier;         // arrivals, monotonic per launch
+    // cache line 0: grid-barrier group arrivals (atomics) and the abort flag
+    unsigned int barrier;         // groups arrived, monotonic per launch
     int abort;                    // set when a bounded wait ran out
     unsigned int pad0[30];
-    // cache line 1: grid-barrier release generation (polled by waiting CTAs)
-    unsigned int bar_gen;
-    unsigned int pad1[31];
     // counters and statistics
     int count[4];                 // active-list sizes (3 rotating lists) + spare
     int status;                   // latched gbp_status of the last device phase
@@ -426,48 +423,71 @@ __device__ __forceinline__ double ld_relaxed_f64(const double *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v)
+__device__ __forceinline__ void st_relaxed_u32(unsigned int *p, unsigned int v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid-wide barrier number `gen` (1, 2, ...) of a cooperative launch.  Each
-// CTA's thread 0 adds one arrival; the last arrival of this generation
-// publishes `gen` on a separate cache line, which the others poll (so the
-// polls do not contend with the arrival atomics).  The wait is bounded:
-// about 2^22 polls with a short sleep each; on timeout the abort flag and
-// GBP_ERR_TIMEOUT are set and every CTA leaves.  Returns false on abort.
-__device__ __forceinline__ bool grid_barrier(Control *ctl, unsigned int gen)
+// Grid-wide barrier number `gen` (1, 2, ...) of a cooperative launch, in two
+// levels: the CTAs form groups of gs (16, more for grids above 2048 CTAs);
+// each group has an arrival counter and a release word on their own cache
+// lines, so arrivals and polls spread over the groups' lines instead of all
+// CTAs hitting one word.  The last CTA of a group adds one arrival to the grid
+// counter (ctl->barrier); the last group's closes the barrier by releasing
+// every group's word.  The wait is bounded: about 2^22 polls with a short
+// sleep each; on timeout the abort flag and GBP_ERR_TIMEOUT are set and every
+// CTA leaves.  Returns false on abort.  grp: GBP_BAR_GROUPS zeroed entries
+// per launch.
+struct BarGroup {
+    unsigned int arr;
+    unsigned int pad0[31];
+    unsigned int gen;
+    unsigned int pad1[31];
+};
+constexpr unsigned int GBP_BAR_GROUPS = 128;
+
+__device__ __forceinline__ bool grid_barrier(Control *ctl, BarGroup *grp, unsigned int gen)
 {
-    __shared__ int s_ok;
+    __shared__ int s_ok2;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        const unsigned int nblk = gridDim.x;
+        const unsigned int gs = max(16u, (nblk + GBP_BAR_GROUPS - 1) / GBP_BAR_GROUPS);
+        const unsigned int ng = (nblk + gs - 1) / gs;
+        const unsigned int g = blockIdx.x / gs;
+        const unsigned int size = min(gs, nblk - g * gs);
         __threadfence();
-        const unsigned int arrived = atomicAdd(&ctl->barrier, 1u) + 1u;
-        if (arrived == gen * gridDim.x) {
-            st_release_u32(&ctl->bar_gen, gen);
-        } else {
-            unsigned int spins = 0;
-            while (ld_acquire_u32(&ctl->bar_gen) < gen) {
-                if (ld_relaxed_i32(&ctl->abort)) {
-                    ok = 0;
-                    break;
-                }
-                if (++spins > (1u << 22)) {
-                    atomicExch(&ctl->abort, 1);
-                    atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(20);
+        const unsigned int arrived = atomicAdd(&grp[g].arr, 1u) + 1u;
+        if (arrived == gen * size) {
+            __threadfence();
+            const unsigned int groups = atomicAdd(&ctl->barrier, 1u) + 1u;
+            if (groups == gen * ng) {
+                // one fence, then plain stores (a release pattern for the
+                // waiters' acquire loads) so the stores issue back to back
+                __threadfence();
+                for (unsigned int h = 0; h < ng; ++h) st_relaxed_u32(&grp[h].gen, gen);
             }
         }
+        unsigned int spins = 0;
+        while (ld_acquire_u32(&grp[g].gen) < gen) {
+            if (ld_relaxed_i32(&ctl->abort)) {
+                ok = 0;
+                break;
+            }
+            if (++spins > (1u << 22)) {
+                atomicExch(&ctl->abort, 1);
+                atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+            __nanosleep(20);
+        }
         __threadfence();
-        s_ok = ok;
+        s_ok2 = ok;
     }
     __syncthreads();
-    return s_ok != 0;
+    return s_ok2 != 0;
 }
 
 // warp-aggregated append of `pred` lanes to list (returns nothing)

@@ -63,6 +63,7 @@ struct gbp_ctx {
     int2 *pc = nullptr;  // FIM state: (value bits, iteration of the last change) per vertex entry
     unsigned long long *keys = nullptr;
     gbp::Control *ctl = nullptr;
+    gbp::BarGroup *bar_grp = nullptr;  // group words of the two-level grid barrier
     gbp::Control *h_ctl = nullptr;  // pinned
     int last_mode = 0, last_nf = 0;
     int64_t param_gen = 0, solve_gen = -1;
