@@ -94,9 +94,14 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
     int k = 1;
     int fb_local = 0;
     unsigned int my_faces = 0;
+    __shared__ int s_ncand;
     for (; k <= a.max_iters; ++k) {
         const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
-        const int n_cand = ld_relaxed_i32(&a.ctl->count[cur]);
+        // one read of the list size per CTA (all warps reading the one word
+        // queue at its L2 slice)
+        if (threadIdx.x == 0) s_ncand = ld_relaxed_i32(&a.ctl->count[cur]);
+        __syncthreads();
+        const int n_cand = s_ncand;
         if (a.trace && blockIdx.x == 0 && threadIdx.x == 0) {
             unsigned long long tns;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tns));
