@@ -477,14 +477,14 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             const int pos = base + incl - npend;
             for (int k = 0; k < npend; ++k) st_relaxed_u64(&queue[pos + k], pend[k]);
         }
-        // retire the chains that ended: their pushes are counted first
+        // retire the chains that ended.  No fence: their pushes are atomics
+        // that have returned, the items they queued were counted before, and
+        // nothing in this loop reads the other writes (mu, proc, gradients),
+        // which the grid barrier after the loop orders.
         const unsigned int ends = __ballot_sync(0xffffffffu, ended);
         if (ends) {
             __syncwarp();
-            if (lane == 0) {
-                __threadfence();
-                atomicSub(&a.ctl->q_active, __popc(ends));
-            }
+            if (lane == 0) atomicSub(&a.ctl->q_active, __popc(ends));
         }
         if (__ballot_sync(0xffffffffu, v >= 0)) {
             idle_spins = 0;
