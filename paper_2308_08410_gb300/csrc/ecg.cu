@@ -12,7 +12,6 @@
 
 namespace gbp {
 
-constexpr int ECG_NL = 16;   // max leads
 constexpr int ECG_CH = 256;  // vertices staged per chunk
 
 // The accurate expf and an IEEE division: the ECG is a sum of up to 10^6

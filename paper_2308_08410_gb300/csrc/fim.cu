@@ -54,9 +54,6 @@ struct FimArgs {
 #ifndef GBP_FIM_R
 #define GBP_FIM_R 1  // faces per lane fetched together
 #endif
-#ifndef GBP_FIM_DYN
-#define GBP_FIM_DYN 0  // warps fetch active vertices from a counter (else a fixed stride)
-#endif
 #ifndef GBP_FIM_BLOCK
 #define GBP_FIM_BLOCK 256  // threads per CTA
 #endif
@@ -69,16 +66,144 @@ constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
 constexpr int FIM_MINB = GBP_FIM_MINB;
 constexpr int FIM_CAP = 2048;  // per-CTA append buffer (overflow goes straight to global)
 
+// One active vertex (entry g of the list) handled by a group of G lanes:
+// its faces in rounds of G, the (value, code) minimum over the group, the
+// update of its state and the activation of its neighbours for k + 1.
+template <int MODE, int G>
+__device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int64_t g, bool act, const int *__restrict__ list,
+                                           int *nlist, int nxt, int *s_list, int *s_n, int &fb_local,
+                                           unsigned int &my_faces)
+{
+    const int64_t n_v = a.n_v;
+    const int sub = threadIdx.x & (G - 1);
+    // entry gi = b * n_v + i: vertex i of problem b
+    int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0, chg_old = 0;
+    int64_t toff = 0;
+    float phi_old = 0.f;
+    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (act) {
+        gi = __ldcg(&list[g]);
+        const int b = gi / (int)n_v;
+        boff = b * (int)n_v;
+        toff = (int64_t)b * a.n_t;
+        i = gi - boff;
+        const int2 own = FIM_LD(&a.pc[gi]);
+        phi_old = __int_as_float(own.x);
+        chg_old = own.y;
+        beg = __ldg(&a.n2t_ptr[i]);
+        end = __ldg(&a.n2t_ptr[i + 1]);
+        nb = __ldg(&a.n2n_ptr[i]);
+        ne = __ldg(&a.n2n_ptr[i + 1]);
+        xi = __ldg(&a.xyz[i]);
+    }
+    const int maxdeg = __reduce_max_sync(0xffffffffu, end - beg);
+    float best = GBP_INF;
+    int best_code = 0x7fffffff;
+    // FIM_R faces per lane at a time: their adjacency, tets and face
+    // values are fetched together (three dependent loads for all of
+    // them), then the masked ones are solved
+    for (int e0 = 0; e0 < maxdeg; e0 += G * FIM_R) {
+        // the face record (face vertex ids, code), then each face
+        // vertex's packed value and change stamp
+        int4 fr[FIM_R];
+#pragma unroll
+        for (int r = 0; r < FIM_R; ++r) {
+            const int e = beg + e0 + r * G + sub;
+            fr[r] = e < end ? __ldg(&a.frec[e]) : make_int4(0, 0, 0, -1);
+        }
+        float ph[FIM_R][3];
+        bool mk[FIM_R];
+#pragma unroll
+        for (int r = 0; r < FIM_R; ++r) {
+            mk[r] = false;
+            ph[r][0] = ph[r][1] = ph[r][2] = GBP_INF;
+            if (fr[r].w >= 0) {
+                const int2 q0 = FIM_LD(&a.pc[boff + fr[r].x]), q1 = FIM_LD(&a.pc[boff + fr[r].y]),
+                           q2 = FIM_LD(&a.pc[boff + fr[r].z]);
+                ph[r][0] = __int_as_float(q0.x);
+                ph[r][1] = __int_as_float(q1.x);
+                ph[r][2] = __int_as_float(q2.x);
+                mk[r] = max(q0.y, max(q1.y, q2.y)) >= k - 1;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < FIM_R; ++r) {
+            if (!mk[r]) continue;
+            const int code_r = fr[r].w;
+            const int j = code_r >> 2, s = code_r & 3;
+            ++my_faces;
+            // metric: the fibre shared by the batch, the velocity terms of this problem
+            const float4 fj = __ldg(&a.tf[j]);
+            const float2 vj = __ldg(&a.tv[toff + j]);
+            const float4 m = make_float4(fj.x, fj.y, fj.z, vj.x);
+            const float sd = vj.y;
+            const float4 x0 = __ldg(&a.xyz[fr[r].x]), x1 = __ldg(&a.xyz[fr[r].y]),
+                         x2 = __ldg(&a.xyz[fr[r].z]);
+            float3 p[3];
+            p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
+            p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
+            p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
+            LocalRes res;
+            if (MODE == GBP_LOCAL_FISTA) {
+                const float4 Lq = __ldg(&a.tlip[toff + j]);
+                const float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
+                res = local_fista(p, ph[r], Lv, a.n_f);
+            } else {
+                res = local_exact(p, ph[r], &fb_local);
+            }
+            if (res.v < best || (res.v == best && code_r < best_code)) {
+                best = res.v;
+                best_code = code_r;
+            }
+        }
+    }
+    // lexicographic (value, code) minimum over the group
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) {
+        const float ov = __shfl_xor_sync(0xffffffffu, best, off);
+        const int oc = __shfl_xor_sync(0xffffffffu, best_code, off);
+        if (ov < best || (ov == best && oc < best_code)) {
+            best = ov;
+            best_code = oc;
+        }
+    }
+    bool changed = false;
+    if (act && best < phi_old) {
+        changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
+        if (sub == 0) {
+            // value and change stamp in one 8-byte store: readers see a pair
+            a.pc[gi] = make_int2(__float_as_int(best), changed ? k : chg_old);
+            a.rec[gi].x = best_code;
+        }
+    }
+    // activate the neighbours of changed vertices for iteration k+1
+    if (!changed) nb = ne = 0;
+    const int maxn = __reduce_max_sync(0xffffffffu, ne - nb);
+    for (int e0 = 0; e0 < maxn; e0 += G) {
+        const int e = nb + e0 + sub;
+        if (e < ne) {
+            const int m = boff + __ldg(&a.n2n[e]);
+            if (atomicMax(&a.stamp[m], k + 1) < k + 1) {
+                const int pos = atomicAdd(s_n, 1);
+                if (pos < FIM_CAP) {
+                    s_list[pos] = m;
+                } else {
+                    nlist[atomicAdd(&a.ctl->count[nxt], 1)] = m;
+                }
+            }
+        }
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
 {
     const int lane = threadIdx.x & 31;
-    const int sub = lane & (FIM_G - 1);
-    const int gl = lane & ~(FIM_G - 1);  // first lane of this group
     const int groups_per_block = blockDim.x / FIM_G;
     const int64_t ggroup = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / FIM_G;
     const int64_t ngroups = (int64_t)gridDim.x * groups_per_block;
-    const int64_t n_v = a.n_v;
+    const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
     __shared__ int s_list[FIM_CAP];
     __shared__ int s_n, s_cnt, s_base;
     __shared__ unsigned long long s_cand, s_faces;
@@ -116,137 +241,20 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
         }
         const int *list = a.lists + (int64_t)cur * a.n_tot;
         int *nlist = a.lists + (int64_t)nxt * a.n_tot;
-#if GBP_FIM_DYN
-        for (;;) {
-            int wbase = 0;
-            if (lane == 0) wbase = atomicAdd(&a.ctl->fim_fetch[cur], 32 / FIM_G);
-            wbase = __shfl_sync(0xffffffffu, wbase, 0);
-            if (wbase >= n_cand) break;
-            const int64_t g = wbase + lane / FIM_G;
-            const bool act = g < n_cand;
-#else
-        for (int64_t g = ggroup;; g += ngroups) {
-            const bool act = g < n_cand;
-            if (!__any_sync(0xffffffffu, act)) break;
-#endif
-            // entry gi = b * n_v + i: vertex i of problem b
-            int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0, chg_old = 0;
-            int64_t toff = 0;
-            float phi_old = 0.f;
-            float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (act) {
-                gi = __ldcg(&list[g]);
-                const int b = gi / (int)n_v;
-                boff = b * (int)n_v;
-                toff = (int64_t)b * a.n_t;
-                i = gi - boff;
-                const int2 own = FIM_LD(&a.pc[gi]);
-                phi_old = __int_as_float(own.x);
-                chg_old = own.y;
-                beg = __ldg(&a.n2t_ptr[i]);
-                end = __ldg(&a.n2t_ptr[i + 1]);
-                nb = __ldg(&a.n2n_ptr[i]);
-                ne = __ldg(&a.n2n_ptr[i + 1]);
-                xi = __ldg(&a.xyz[i]);
+        // a front smaller than a third of the 8-lane groups: one warp per
+        // vertex, so a vertex's faces take one round instead of three
+        if ((int64_t)n_cand * 3 <= ngroups) {
+            for (int64_t g = gwarp;; g += nwarps) {
+                const bool act = g < n_cand;
+                if (!__any_sync(0xffffffffu, act)) break;
+                fim_vertex<MODE, 32>(a, k, g, act, list, nlist, nxt, s_list, &s_n, fb_local, my_faces);
             }
-            const int maxdeg = __reduce_max_sync(0xffffffffu, end - beg);
-            float best = GBP_INF;
-            int best_code = 0x7fffffff;
-            // FIM_R faces per lane at a time: their adjacency, tets and face
-            // values are fetched together (three dependent loads for all of
-            // them), then the masked ones are solved
-            for (int e0 = 0; e0 < maxdeg; e0 += FIM_G * FIM_R) {
-                // the face record (face vertex ids, code), then each face
-                // vertex's packed value and change stamp
-                int4 fr[FIM_R];
-#pragma unroll
-                for (int r = 0; r < FIM_R; ++r) {
-                    const int e = beg + e0 + r * FIM_G + sub;
-                    fr[r] = e < end ? __ldg(&a.frec[e]) : make_int4(0, 0, 0, -1);
-                }
-                float ph[FIM_R][3];
-                bool mk[FIM_R];
-#pragma unroll
-                for (int r = 0; r < FIM_R; ++r) {
-                    mk[r] = false;
-                    ph[r][0] = ph[r][1] = ph[r][2] = GBP_INF;
-                    if (fr[r].w >= 0) {
-                        const int2 q0 = FIM_LD(&a.pc[boff + fr[r].x]), q1 = FIM_LD(&a.pc[boff + fr[r].y]),
-                                   q2 = FIM_LD(&a.pc[boff + fr[r].z]);
-                        ph[r][0] = __int_as_float(q0.x);
-                        ph[r][1] = __int_as_float(q1.x);
-                        ph[r][2] = __int_as_float(q2.x);
-                        mk[r] = max(q0.y, max(q1.y, q2.y)) >= k - 1;
-                    }
-                }
-#pragma unroll
-                for (int r = 0; r < FIM_R; ++r) {
-                    if (!mk[r]) continue;
-                    const int code_r = fr[r].w;
-                    const int j = code_r >> 2, s = code_r & 3;
-                    ++my_faces;
-                    // metric: the fibre shared by the batch, the velocity terms of this problem
-                    const float4 fj = __ldg(&a.tf[j]);
-                    const float2 vj = __ldg(&a.tv[toff + j]);
-                    const float4 m = make_float4(fj.x, fj.y, fj.z, vj.x);
-                    const float sd = vj.y;
-                    const float4 x0 = __ldg(&a.xyz[fr[r].x]), x1 = __ldg(&a.xyz[fr[r].y]),
-                                 x2 = __ldg(&a.xyz[fr[r].z]);
-                    float3 p[3];
-                    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
-                    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
-                    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
-                    LocalRes res;
-                    if (MODE == GBP_LOCAL_FISTA) {
-                        const float4 Lq = __ldg(&a.tlip[toff + j]);
-                        const float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
-                        res = local_fista(p, ph[r], Lv, a.n_f);
-                    } else {
-                        res = local_exact(p, ph[r], &fb_local);
-                    }
-                    if (res.v < best || (res.v == best && code_r < best_code)) {
-                        best = res.v;
-                        best_code = code_r;
-                    }
-                }
+        } else {
+            for (int64_t g = ggroup;; g += ngroups) {
+                const bool act = g < n_cand;
+                if (!__any_sync(0xffffffffu, act)) break;
+                fim_vertex<MODE, FIM_G>(a, k, g, act, list, nlist, nxt, s_list, &s_n, fb_local, my_faces);
             }
-            // lexicographic (value, code) minimum over the group
-#pragma unroll
-            for (int off = FIM_G / 2; off > 0; off >>= 1) {
-                const float ov = __shfl_xor_sync(0xffffffffu, best, off);
-                const int oc = __shfl_xor_sync(0xffffffffu, best_code, off);
-                if (ov < best || (ov == best && oc < best_code)) {
-                    best = ov;
-                    best_code = oc;
-                }
-            }
-            bool changed = false;
-            if (act && best < phi_old) {
-                changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
-                if (sub == 0) {
-                    // value and change stamp in one 8-byte store: readers see a pair
-                    a.pc[gi] = make_int2(__float_as_int(best), changed ? k : chg_old);
-                    a.rec[gi].x = best_code;
-                }
-            }
-            // activate the neighbours of changed vertices for iteration k+1
-            if (!changed) nb = ne = 0;
-            const int maxn = __reduce_max_sync(0xffffffffu, ne - nb);
-            for (int e0 = 0; e0 < maxn; e0 += FIM_G) {
-                const int e = nb + e0 + sub;
-                if (e < ne) {
-                    const int m = boff + __ldg(&a.n2n[e]);
-                    if (atomicMax(&a.stamp[m], k + 1) < k + 1) {
-                        const int pos = atomicAdd(&s_n, 1);
-                        if (pos < FIM_CAP) {
-                            s_list[pos] = m;
-                        } else {
-                            nlist[atomicAdd(&a.ctl->count[nxt], 1)] = m;
-                        }
-                    }
-                }
-            }
-            (void)gl;
         }
         // flush the CTA's appends with one global reservation
         __syncthreads();
