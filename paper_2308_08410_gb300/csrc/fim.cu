@@ -236,7 +236,6 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
         if (n_cand == 0) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             a.ctl->count[nn] = 0;
-            a.ctl->fim_fetch[nxt] = 0;  // last used at k-2, next used at k+1
             s_cand += (unsigned long long)n_cand;
         }
         const int *list = a.lists + (int64_t)cur * a.n_tot;

@@ -39,8 +39,6 @@ struct Control {
     int padq1[31];
     int q_active;                 // chains queued or in progress
     int padq2[31];
-    int fim_fetch[3];             // FIM work counters (rotating with the active lists)
-    int padq3[29];
     int adj_levels;
     int adj_cycle_nodes;
     int adj_cycle_iters;
