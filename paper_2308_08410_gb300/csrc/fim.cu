@@ -111,6 +111,13 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int64_t g, b
             const int e = beg + e0 + r * G + sub;
             fr[r] = e < end ? __ldg(&a.frec[e]) : make_int4(0, 0, 0, -1);
         }
+        // the face's per-problem velocity terms (the one input of the solve
+        // that is mostly not in L2 once a batch is in flight) depend only on
+        // the face record: issued before the face values come back
+        float2 vj[FIM_R];
+#pragma unroll
+        for (int r = 0; r < FIM_R; ++r)
+            if (fr[r].w >= 0) vj[r] = __ldg(&a.tv[toff + (fr[r].w >> 2)]);
         float ph[FIM_R][3];
         bool mk[FIM_R];
 #pragma unroll
@@ -134,9 +141,8 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int64_t g, b
             ++my_faces;
             // metric: the fibre shared by the batch, the velocity terms of this problem
             const float4 fj = __ldg(&a.tf[j]);
-            const float2 vj = __ldg(&a.tv[toff + j]);
-            const float4 m = make_float4(fj.x, fj.y, fj.z, vj.x);
-            const float sd = vj.y;
+            const float4 m = make_float4(fj.x, fj.y, fj.z, vj[r].x);
+            const float sd = vj[r].y;
             const float4 x0 = __ldg(&a.xyz[fr[r].x]), x1 = __ldg(&a.xyz[fr[r].y]),
                          x2 = __ldg(&a.xyz[fr[r].z]);
             float3 p[3];
