@@ -55,16 +55,22 @@ struct FimArgs {
 #define GBP_FIM_R 1  // faces per lane fetched together
 #endif
 #ifndef GBP_FIM_BLOCK
-#define GBP_FIM_BLOCK 256  // threads per CTA
+#define GBP_FIM_BLOCK 1024  // threads per CTA
 #endif
 constexpr int FIM_G = GBP_FIM_G;
 constexpr int FIM_R = GBP_FIM_R;
 constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
+// One CTA of 1024 threads per SM (64 registers): the same 32 warps per SM as
+// four CTAs of 256, with a quarter of the grid barrier's arrivals and each
+// CTA's appends gathered over four times the vertices
 #ifndef GBP_FIM_MINB
-#define GBP_FIM_MINB 4  // CTAs per SM (64 registers at 256 threads)
+#define GBP_FIM_MINB 1  // CTAs per SM
 #endif
 constexpr int FIM_MINB = GBP_FIM_MINB;
-constexpr int FIM_CAP = 2048;  // per-CTA append buffer (overflow goes straight to global)
+#ifndef GBP_FIM_CAP
+#define GBP_FIM_CAP 2048  // per-CTA append buffer (overflow goes straight to global)
+#endif
+constexpr int FIM_CAP = GBP_FIM_CAP;
 
 // One active vertex (entry g of the list) handled by a group of G lanes:
 // its faces in rounds of G, the (value, code) minimum over the group, the
