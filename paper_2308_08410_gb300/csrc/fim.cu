@@ -67,8 +67,12 @@ constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
 #define GBP_FIM_MINB 1  // CTAs per SM
 #endif
 constexpr int FIM_MINB = GBP_FIM_MINB;
+// Per-CTA append buffer for the next active list; appends beyond it go
+// straight to the global list during the iteration.  A small buffer leaves
+// less to the flush at the end of the iteration, which every CTA does
+// before the grid barrier (16 problems: 512 entries 27.0 ms, 2048 28.2 ms).
 #ifndef GBP_FIM_CAP
-#define GBP_FIM_CAP 2048  // per-CTA append buffer (overflow goes straight to global)
+#define GBP_FIM_CAP 512
 #endif
 constexpr int FIM_CAP = GBP_FIM_CAP;
 
