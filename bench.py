@@ -112,6 +112,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(seconds, dist=None, device=None):
+    """The job's time when every rank runs one replica: the slowest rank's
+    time (all_reduce MAX; the ranks' own time on one process)."""
+    if dist is None:
+        return float(seconds)
+    import torch
+    tt = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Whole-job throughput: world ranks each processed units_per_rank in
+    `seconds`, the max-over-ranks time."""
+    return world * units_per_rank / seconds
+
+
 def build_inputs(n, seed=0):
     from paper_2308_08410_gb300 import synth as S
     p = S.make_c3(n=n, seed=seed)
@@ -260,11 +277,8 @@ def main():
             s_ms.append(e0.elapsed_time(e1))
         single = {"value": world * 1e3 * len(s_ms) / sum(s_ms), "unit": "evals/s",
                   "ms_per_step": sum(s_ms) / len(s_ms), "batch": 1}
-    total_s = sum(ms_steps) / 1e3
+    total_s = max_over_ranks(sum(ms_steps) / 1e3, dist, dev)
     if dist is not None:
-        tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
         dist.barrier()
 
     # e2e: the same evaluation from host buffers through the host entry points
@@ -289,12 +303,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e2e_step()
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
-        e2e = {"value": world * B * args.steps / e2e_s, "unit": "evals/s",
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        e2e = {"value": job_throughput(B * args.steps, world, e2e_s), "unit": "evals/s",
                "h2d_bytes_per_step": int(sum(h.nbytes for h in hin)),
                "d2h_bytes_per_step": int(sum(h.nbytes for h in hout.values()))}
     if not args.no_e2e and B == 1:
@@ -308,13 +318,9 @@ def main():
         for _ in range(args.steps):
             h_out = ctx.forward_backward_host(cf_np, ct_np, target_np, p.tmpl, t=ons.t, opts=opts,
                                               precision=prec, out=h_out)
-        e2e_s = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dist, dev)
         n_t, K, NT = p.mesh.n_t, p.onsets.K, target_np.size
-        e2e = {"value": world * args.steps / e2e_s, "unit": "evals/s",
+        e2e = {"value": job_throughput(args.steps, world, e2e_s), "unit": "evals/s",
                "h2d_bytes_per_step": int(4 * (2 * n_t + K + NT)),
                "d2h_bytes_per_step": int(4 * (1 + 2 * n_t + 4 * K))}
 
@@ -331,7 +337,7 @@ def main():
     achieved = face_updates * BYTES_PER_TET_UPDATE / (fim_ms / 1e3) / 1e9
     adj_achieved = B * p.mesh.n_v * BYTES_PER_ADJ_NODE / (adj_ms / 1e3) / 1e9
     ms_per_step = 1e3 * total_s / steps
-    value = world * B * steps / total_s
+    value = job_throughput(B * steps, world, total_s)
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         from oracle import oracle as O

@@ -1,0 +1,75 @@
+"""The benchmark's multi-rank host logic on CPU: one replica per rank, the
+job's time is the slowest rank's (all_reduce MAX over two gloo ranks), the
+value is every rank's units over that time, and under torchrun only rank 0
+runs the oracle arm while the other ranks leave without work."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+WORKER = r"""
+import json, os, sys
+sys.path.insert(0, os.environ["BENCH_ROOT"])
+import torch.distributed as dist
+import bench
+dist.init_process_group("gloo", init_method="env://")
+rank = dist.get_rank()
+own = [3.0, 5.0][rank]           # this rank's timed region, seconds
+t = bench.max_over_ranks(own, dist, "cpu")
+v = bench.job_throughput(16 * 20, dist.get_world_size(), t)
+print(json.dumps({"rank": rank, "t": t, "value": v}))
+dist.barrier()
+dist.destroy_process_group()
+"""
+
+
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_max_over_two_gloo_ranks():
+    pytest.importorskip("torch")
+    port = free_port()
+    procs = []
+    for r in range(2):
+        env = dict(os.environ, RANK=str(r), WORLD_SIZE="2", MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port),
+                   BENCH_ROOT=ROOT)
+        procs.append(subprocess.Popen([sys.executable, "-c", WORKER], env=env, stdout=subprocess.PIPE,
+                                      stderr=subprocess.PIPE, text=True))
+    outs = []
+    for p in procs:
+        o, e = p.communicate(timeout=120)
+        assert p.returncode == 0, e
+        outs.append(json.loads(o.strip().splitlines()[-1]))
+    for o in outs:
+        assert o["t"] == 5.0                          # the slowest rank's time on every rank
+        assert o["value"] == pytest.approx(2 * 16 * 20 / 5.0)
+
+
+def test_single_process_and_arithmetic():
+    assert bench.max_over_ranks(2.5) == 2.5
+    assert bench.job_throughput(320, 1, 0.5) == 640.0
+    assert bench.job_throughput(320, 4, 2.0) == 640.0
+
+
+def test_reference_arm_on_other_ranks_does_nothing(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    called = []
+    monkeypatch.setattr(bench, "run_reference", lambda *a: called.append(a))
+    bench.main()
+    assert called == [] and capsys.readouterr().out == ""
+    monkeypatch.setenv("RANK", "0")
+    bench.main()
+    assert len(called) == 1 and called[0][1] == 2     # rank 0 runs it, with the world size
