@@ -320,6 +320,25 @@ def test_errors(ctx):
     assert ei.value.status == 8
 
 
+def test_empty_inputs_are_refused(ctx):
+    """Zero-sized inputs (a mesh without vertices or tets, no onsets) are
+    refused on the host with GBP_ERR_INVALID_ARG before any state changes:
+    the context still solves the problem it holds."""
+    p = jittered_c1(n=6, seed=1)
+    gbp.setup_problem(ctx, p)
+    with pytest.raises(gbp.GbpError) as ei:
+        ctx.upload_mesh(np.zeros((0, 3), np.float32), np.zeros((0, 4), np.int32))
+    assert ei.value.status == 1
+    with pytest.raises(gbp.GbpError) as ei:
+        ctx.set_onsets(gbp.ONSET_NODAL, dev(np.zeros(0, np.int32), np.int32), dev(np.zeros(0)))
+    assert ei.value.status == 1
+    phi, _, _ = ctx.eikonal_solve()
+    assert ctx.stats()["status"] == 0
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    rel = np.abs(phi.cpu().numpy() - ref["phi"]) / np.maximum(1.0, ref["phi"])
+    assert rel.max() < 1e-4
+
+
 # ---------------------------------------------------------------------------
 # BF16 tensor-core ECG
 # ---------------------------------------------------------------------------
