@@ -39,3 +39,61 @@ def test_create_fails_cleanly_without_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(RuntimeError):
         gbp.Context(0)
+
+
+PROBE = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "gbp.h"
+#define F(T, m) printf("%s.%s %zu %zu\n", #T, #m, offsetof(T, m), sizeof(((T *)0)->m))
+int main(void)
+{
+    printf("sizeof gbp_solve_opts %zu\n", sizeof(gbp_solve_opts));
+    printf("sizeof gbp_solve_stats %zu\n", sizeof(gbp_solve_stats));
+    printf("sizeof gbp_template %zu\n", sizeof(gbp_template));
+    F(gbp_solve_opts, local_solver); F(gbp_solve_opts, n_f); F(gbp_solve_opts, eps); F(gbp_solve_opts, max_iters);
+    F(gbp_solve_stats, iterations); F(gbp_solve_stats, candidates); F(gbp_solve_stats, face_updates);
+    F(gbp_solve_stats, fp64_fallbacks); F(gbp_solve_stats, unreached); F(gbp_solve_stats, adj_levels);
+    F(gbp_solve_stats, adj_cycle_nodes); F(gbp_solve_stats, adj_cycle_iters); F(gbp_solve_stats, status);
+    F(gbp_solve_stats, reserved); F(gbp_solve_stats, adj_dataflow_ms); F(gbp_solve_stats, adj_cycle_ms);
+    F(gbp_template, K0); F(gbp_template, K1); F(gbp_template, tau); F(gbp_template, t0); F(gbp_template, dt);
+    F(gbp_template, T);
+    printf("const LOCAL_EXACT %d\nconst LOCAL_FISTA %d\n", GBP_LOCAL_EXACT, GBP_LOCAL_FISTA);
+    printf("const ONSET_NODAL %d\nconst ONSET_ELEMENT %d\n", GBP_ONSET_NODAL, GBP_ONSET_ELEMENT);
+    printf("const PREC_FP32 %d\nconst PREC_BF16 %d\n", GBP_PREC_FP32, GBP_PREC_BF16);
+    printf("const STATUS_LAST %d\n", (int)GBP_ERR_NO_MEMORY);
+    return 0;
+}
+"""
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """The ctypes structures and constants of gbp.py have the header's field
+    offsets, sizes and enum values (a C probe compiled with gcc prints them)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "probe.c"
+    src.write_text(PROBE)
+    exe = tmp_path / "probe"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    structs = {"gbp_solve_opts": gbp.SolveOpts, "gbp_solve_stats": gbp.SolveStats, "gbp_template": gbp.Template}
+    seen = 0
+    for line in filter(None, out):
+        a, *vals = line.split()
+        if a == "sizeof":
+            assert ctypes.sizeof(structs[vals[0]]) == int(vals[1]), line
+        elif a == "const":
+            if vals[0] == "STATUS_LAST":
+                assert max(gbp._STATUS) == int(vals[1])
+            else:
+                assert getattr(gbp, vals[0]) == int(vals[1]), line
+        else:
+            sname, field = a.split(".")
+            desc = getattr(structs[sname], field)
+            assert (desc.offset, desc.size) == (int(vals[0]), int(vals[1])), line
+        seen += 1
+    assert seen == 3 + 22 + 7
