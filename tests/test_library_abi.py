@@ -97,3 +97,45 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
             assert (desc.offset, desc.size) == (int(vals[0]), int(vals[1])), line
         seen += 1
     assert seen == 3 + 22 + 7
+
+
+def _c_kind(decl):
+    decl = decl.strip()
+    if "*" in decl:
+        return "ptr"
+    toks = decl.replace("const ", "").split()
+    t = toks[0] if toks else "void"
+    return {"int64_t": "i64", "int32_t": "i32", "int": "i32", "float": "f32", "double": "f64",
+            "gbp_status": "i32", "void": None}[t]
+
+
+def _ctypes_kind(t):
+    if t is None:
+        return None
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "ptr"
+    if t is ctypes.c_float:
+        return "f32"
+    if t is ctypes.c_double:
+        return "f64"
+    return "i%d" % (8 * ctypes.sizeof(t))
+
+
+def test_binding_signatures_match_the_header():
+    """Every prototype of include/gbp.h has the arity, argument widths
+    (pointer / 32- / 64-bit integer / float) and return kind that the
+    binding's argtypes and restype give it."""
+    hdr = open(os.path.join(ROOT, "include", "gbp.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    hdr = re.sub(r"//[^\n]*", "", hdr)
+    protos = re.findall(r"([A-Za-z_][\w \t\*]*?)\b(gbp_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", hdr)
+    lib = gbp.load()
+    checked = 0
+    for ret, name, params in protos:
+        params = " ".join(params.split())
+        cargs = [] if params in ("", "void") else [_c_kind(p) for p in params.split(",")]
+        fn = getattr(lib, name)
+        assert [_ctypes_kind(a) for a in fn.argtypes] == cargs, name
+        assert _ctypes_kind(fn.restype) == _c_kind(ret.replace("static", "")), name
+        checked += 1
+    assert checked == len(gbp.exported_symbols())
