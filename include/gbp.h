@@ -144,6 +144,18 @@ gbp_status gbp_upload_mesh(gbp_ctx *ctx, const float *xyz, int64_t n_v, const in
 gbp_status gbp_upload_mesh_2d(gbp_ctx *ctx, const float *xy, int64_t n_v, const int32_t *tris,
                               int64_t n_t);
 
+/* Host-only validation (no context, no device, nothing allocated): the
+ * checks gbp_upload_mesh / gbp_upload_mesh_2d make before they build
+ * anything, on the same host arrays.  Tets: n_v >= 4, n_t >= 1, coordinates
+ * finite, vertex ids in [0, n_v) and distinct within a tet, signed volume
+ * above 1e-15 diag^3 (diag = bounding-box diagonal; right-handed).
+ * Triangles: n_v >= 3, the same id checks, signed area above 1e-12 ext^2
+ * (ext = larger bounding-box side; counter-clockwise).  Returns GBP_OK,
+ * GBP_ERR_INVALID_ARG (NULL pointer, sizes out of range: n_v < 2^30 and
+ * n_t < 2^29) or GBP_ERR_BAD_MESH. */
+gbp_status gbp_check_mesh(const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t);
+gbp_status gbp_check_mesh_2d(const float *xy, int64_t n_v, const int32_t *tris, int64_t n_t);
+
 /* Fibre directions f_j: device float32 [n_t][3] (normalised here; a zero
  * vector is GBP_ERR_NOT_SPD at the next velocity update). Copied. */
 gbp_status gbp_set_fibres(gbp_ctx *ctx, const float *fib);

@@ -272,13 +272,13 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
                              int64_t n_real, int dim);
 static cudaError_t ensure_batch(gbp_ctx *c, int B);
 
-gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
+// Host validation of a tet mesh: sizes within the limits, coordinates
+// finite, vertex ids in range and distinct within a tet, signed volume above
+// 1e-15 diag^3 (right-handed, not degenerate).
+static gbp_status check_tets(const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
 {
-    if (!c || !xyz || !tets || n_v < 4 || n_t < 1 || n_v >= (1ll << 30) || n_t >= (1ll << 29))
+    if (!xyz || !tets || n_v < 4 || n_t < 1 || n_v >= (1ll << 30) || n_t >= (1ll << 29))
         return GBP_ERR_INVALID_ARG;
-    DeviceGuard g(c->device);
-    cudaStreamSynchronize(c->stream);
-    // validation: ids in range and distinct, positive volume
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int64_t i = 0; i < n_v; ++i)
         for (int r = 0; r < 3; ++r) {
@@ -304,6 +304,58 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
                      e[0][2] * (e[1][0] * e[2][1] - e[1][1] * e[2][0]);
         if (!(det / 6.0 > vtol)) return GBP_ERR_BAD_MESH;
     }
+    return GBP_OK;
+}
+
+// Host validation of a triangle mesh: sizes within the limits, coordinates
+// finite, ids in range and distinct, area above 1e-12 ext^2 counter-clockwise.
+// lo / hi receive the bounding box.
+static gbp_status check_tris(const float *xy, int64_t n_v, const int32_t *tris, int64_t n_t, double lo[2],
+                             double hi[2])
+{
+    if (!xy || !tris || n_v < 3 || n_t < 1 || n_v + 1 >= (1ll << 30) || n_t >= (1ll << 29))
+        return GBP_ERR_INVALID_ARG;
+    lo[0] = lo[1] = 1e300;
+    hi[0] = hi[1] = -1e300;
+    for (int64_t i = 0; i < n_v; ++i)
+        for (int r = 0; r < 2; ++r) {
+            double v = xy[2 * i + r];
+            if (!std::isfinite(v)) return GBP_ERR_BAD_MESH;
+            lo[r] = std::min(lo[r], v);
+            hi[r] = std::max(hi[r], v);
+        }
+    const double ext = std::max(hi[0] - lo[0], hi[1] - lo[1]);
+    const double atol = 1e-12 * ext * ext;
+    for (int64_t j = 0; j < n_t; ++j) {
+        const int32_t *t = tris + 3 * j;
+        for (int q = 0; q < 3; ++q)
+            if (t[q] < 0 || t[q] >= n_v) return GBP_ERR_BAD_MESH;
+        if (t[0] == t[1] || t[0] == t[2] || t[1] == t[2]) return GBP_ERR_BAD_MESH;
+        const double ax = (double)xy[2 * t[1]] - xy[2 * t[0]], ay = (double)xy[2 * t[1] + 1] - xy[2 * t[0] + 1];
+        const double bx = (double)xy[2 * t[2]] - xy[2 * t[0]], by = (double)xy[2 * t[2] + 1] - xy[2 * t[0] + 1];
+        if (!(0.5 * (ax * by - ay * bx) > atol)) return GBP_ERR_BAD_MESH;  // counter-clockwise, not degenerate
+    }
+    return GBP_OK;
+}
+
+gbp_status gbp_check_mesh(const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
+{
+    return check_tets(xyz, n_v, tets, n_t);
+}
+
+gbp_status gbp_check_mesh_2d(const float *xy, int64_t n_v, const int32_t *tris, int64_t n_t)
+{
+    double lo[2], hi[2];
+    return check_tris(xy, n_v, tris, n_t, lo, hi);
+}
+
+gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t)
+{
+    if (!c) return GBP_ERR_INVALID_ARG;
+    const gbp_status st = check_tets(xyz, n_v, tets, n_t);
+    if (st != GBP_OK) return st;
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
     return build_mesh(c, xyz, n_v, tets, n_t, n_v, 3);
 }
 
@@ -429,29 +481,13 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
 
 gbp_status gbp_upload_mesh_2d(gbp_ctx *c, const float *xy, int64_t n_v, const int32_t *tris, int64_t n_t)
 {
-    if (!c || !xy || !tris || n_v < 3 || n_t < 1 || n_v + 1 >= (1ll << 30) || n_t >= (1ll << 29))
-        return GBP_ERR_INVALID_ARG;
+    if (!c) return GBP_ERR_INVALID_ARG;
+    double lo[2], hi[2];
+    const gbp_status st = check_tris(xy, n_v, tris, n_t, lo, hi);
+    if (st != GBP_OK) return st;
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
-    double lo[2] = {1e300, 1e300}, hi[2] = {-1e300, -1e300};
-    for (int64_t i = 0; i < n_v; ++i)
-        for (int r = 0; r < 2; ++r) {
-            double v = xy[2 * i + r];
-            if (!std::isfinite(v)) return GBP_ERR_BAD_MESH;
-            lo[r] = std::min(lo[r], v);
-            hi[r] = std::max(hi[r], v);
-        }
     const double ext = std::max(hi[0] - lo[0], hi[1] - lo[1]);
-    const double atol = 1e-12 * ext * ext;
-    for (int64_t j = 0; j < n_t; ++j) {
-        const int32_t *t = tris + 3 * j;
-        for (int q = 0; q < 3; ++q)
-            if (t[q] < 0 || t[q] >= n_v) return GBP_ERR_BAD_MESH;
-        if (t[0] == t[1] || t[0] == t[2] || t[1] == t[2]) return GBP_ERR_BAD_MESH;
-        const double ax = (double)xy[2 * t[1]] - xy[2 * t[0]], ay = (double)xy[2 * t[1] + 1] - xy[2 * t[0] + 1];
-        const double bx = (double)xy[2 * t[2]] - xy[2 * t[0]], by = (double)xy[2 * t[2] + 1] - xy[2 * t[0] + 1];
-        if (!(0.5 * (ax * by - ay * bx) > atol)) return GBP_ERR_BAD_MESH;  // counter-clockwise, not degenerate
-    }
     // lift: (x, y, 0) and the apex above the centre of the bounding box; any
     // height works (the apex is never reached), the extent keeps the tets well shaped
     std::vector<float> xyz(3 * (n_v + 1));

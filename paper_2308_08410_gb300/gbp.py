@@ -79,6 +79,8 @@ def load():
         "gbp_synchronize": ([P], i32),
         "gbp_upload_mesh": ([P, P, i64, P, i64], i32),
         "gbp_upload_mesh_2d": ([P, P, i64, P, i64], i32),
+        "gbp_check_mesh": ([P, i64, P, i64], i32),
+        "gbp_check_mesh_2d": ([P, i64, P, i64], i32),
         "gbp_set_fibres": ([P, P], i32),
         "gbp_set_velocities": ([P, P, P], i32),
         "gbp_set_leadfield": ([P, P, i32], i32),
@@ -129,7 +131,7 @@ def exported_symbols():
     """Names of the entry points this binding expects the library to export."""
     return [
         "gbp_create", "gbp_destroy", "gbp_set_stream", "gbp_status_string", "gbp_synchronize",
-        "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
+        "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_check_mesh", "gbp_check_mesh_2d", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
         "gbp_set_onsets", "gbp_set_onsets_batch", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
         "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_forward_backward_batch_host", "gbp_local_solve_batch", "gbp_enable_timing",
@@ -170,6 +172,21 @@ def _hptr(a, dtype=None):
 def _f32(a):
     """Host pointer of a float32 array (the host entry points read float32)."""
     return _hptr(a, np.float32)
+
+
+def check_mesh(xyz: np.ndarray, tets: np.ndarray) -> int:
+    """Host-only validation of a tet mesh (gbp_check_mesh): the status
+    gbp_upload_mesh would return for it before building anything."""
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    tets = np.ascontiguousarray(tets, np.int32)
+    return int(load().gbp_check_mesh(_hptr(xyz), xyz.shape[0], _hptr(tets), tets.shape[0]))
+
+
+def check_mesh_2d(xy: np.ndarray, tris: np.ndarray) -> int:
+    """Host-only validation of a triangle mesh (gbp_check_mesh_2d)."""
+    xy = np.ascontiguousarray(xy, np.float32)
+    tris = np.ascontiguousarray(tris, np.int32)
+    return int(load().gbp_check_mesh_2d(_hptr(xy), xy.shape[0], _hptr(tris), tris.shape[0]))
 
 
 def make_opts(local_solver=LOCAL_EXACT, n_f=32, eps=0.0, max_iters=0) -> SolveOpts:
