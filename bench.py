@@ -346,16 +346,7 @@ def main():
                "sample": "one full evaluation of the same workload (FP64 oracle: worklist Gauss-Seidel "
                          "eikonal single-threaded, ECG / misfit OpenMP, SCC adjoint serial)",
                "seconds": t_cpu, "loss_gpu": float(out["loss"].reshape(-1)[0].item()), "loss_oracle": r["loss"]}
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", f"fim_traffic_c3_batch{B}.txt")
-    if os.path.exists(prof):
-        try:
-            with open(prof) as f:
-                tj = json.load(f)
-            if tj.get("kernel_hash") == kernel_hash() and tj.get("batch") == B and tj.get("n") == args.n:
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = stored_traffic(B, args.n)
     line = {
         "metric": METRIC,
         "value": value,
@@ -406,6 +397,21 @@ def kernel_hash() -> str:
         with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def stored_traffic(batch, n, path=None):
+    """DRAM bytes per k_fim launch from the committed ncu summary for this
+    workload, or None when there is none or it was taken on other kernel
+    sources (its kernel_hash differs), another batch size or mesh."""
+    path = path or os.path.join(ROOT, "profiles", f"fim_traffic_c3_batch{batch}.txt")
+    try:
+        with open(path) as f:
+            tj = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if tj.get("kernel_hash") == kernel_hash() and tj.get("batch") == batch and tj.get("n") == n:
+        return tj.get("bytes_per_launch")
+    return None
 
 
 def run_reference(args, world):

@@ -1,7 +1,8 @@
-"""The benchmark's multi-rank host logic on CPU: one replica per rank, the
+"""Host logic of the benchmark on CPU: one replica per rank, the
 job's time is the slowest rank's (all_reduce MAX over two gloo ranks), the
 value is every rank's units over that time, and under torchrun only rank 0
-runs the oracle arm while the other ranks leave without work."""
+runs the oracle arm while the other ranks leave without work; the stored
+ncu traffic figure is reported only for the kernel it was captured on."""
 import json
 import os
 import socket
@@ -73,3 +74,20 @@ def test_reference_arm_on_other_ranks_does_nothing(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "0")
     bench.main()
     assert len(called) == 1 and called[0][1] == 2     # rank 0 runs it, with the world size
+
+
+def test_stored_traffic_applies_only_to_its_kernel(tmp_path):
+    """The ncu traffic figure is reported only for the kernel sources,
+    batch size and mesh it was captured on."""
+    rec = {"kernel": "k_fim", "kernel_hash": bench.kernel_hash(), "batch": 16, "n": 72,
+           "bytes_per_launch": 123456789}
+    f = tmp_path / "t.txt"
+    f.write_text(json.dumps(rec))
+    assert bench.stored_traffic(16, 72, str(f)) == 123456789
+    assert bench.stored_traffic(8, 72, str(f)) is None
+    assert bench.stored_traffic(16, 40, str(f)) is None
+    f.write_text(json.dumps(dict(rec, kernel_hash="0" * 12)))
+    assert bench.stored_traffic(16, 72, str(f)) is None
+    f.write_text("not json")
+    assert bench.stored_traffic(16, 72, str(f)) is None
+    assert bench.stored_traffic(16, 72, str(tmp_path / "missing.txt")) is None
