@@ -156,6 +156,24 @@ gbp_status gbp_upload_mesh_2d(gbp_ctx *ctx, const float *xy, int64_t n_v, const 
 gbp_status gbp_check_mesh(const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t);
 gbp_status gbp_check_mesh_2d(const float *xy, int64_t n_v, const int32_t *tris, int64_t n_t);
 
+/* Host-only (no context, no device): the adjacency gbp_upload_mesh builds
+ * for the FIM and the adjoint, on host arrays.  tets int32 [n_t][4] with ids
+ * in [0, n_v).  Writes *n_faces (= 4 n_t entries of the vertex->tet lists)
+ * and *n_nbr (entries of the vertex->vertex lists); when all five arrays are
+ * non-NULL it also fills them (caller-owned host memory):
+ *   n2t_ptr int32 [n_v + 1], n2t int32 [n_faces]: per vertex the codes
+ *     tet * 4 + slot of its incident tets, in ascending code;
+ *   n2n_ptr int32 [n_v + 1], n2n int32 [n_nbr]: per vertex its neighbours
+ *     through a shared tet, sorted and unique;
+ *   frec int32 [n_faces][4]: per vertex->tet entry, the tet's other three
+ *     vertices in slot order and the code (the FIM's face records).
+ * Call once with NULL arrays for the sizes, then with the arrays.  Errors:
+ * GBP_ERR_INVALID_ARG (NULL tets or size pointers, sizes out of range),
+ * GBP_ERR_BAD_MESH (an id out of range). */
+gbp_status gbp_mesh_adjacency(const int32_t *tets, int64_t n_v, int64_t n_t, int64_t *n_faces,
+                              int64_t *n_nbr, int32_t *n2t_ptr, int32_t *n2t, int32_t *n2n_ptr,
+                              int32_t *n2n, int32_t *frec);
+
 /* Fibre directions f_j: device float32 [n_t][3] (normalised here; a zero
  * vector is GBP_ERR_NOT_SPD at the next velocity update). Copied. */
 gbp_status gbp_set_fibres(gbp_ctx *ctx, const float *fib);

@@ -359,38 +359,42 @@ gbp_status gbp_upload_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int3
     return build_mesh(c, xyz, n_v, tets, n_t, n_v, 3);
 }
 
-// Adjacency, face records and device buffers of a validated tet mesh.
-// Vertices from n_real on (the apex of a lifted triangle mesh) get an empty
-// vertex->tet row and appear in no vertex->vertex row: they are never solved
-// nor activated.
-static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t,
-                             int64_t n_real, int dim)
+// Host adjacency of a validated tet mesh.  Vertices from n_real on (the
+// apex of a lifted triangle mesh) get an empty vertex->tet row and appear in
+// no vertex->vertex row: they are never solved nor activated.
+struct HostAdjacency {
+    std::vector<int> n2t_ptr, n2t;  // vertex -> tet*4 + slot, rows in ascending code
+    std::vector<int> n2n_ptr, n2n;  // vertex -> neighbours through a shared tet, sorted, unique
+    std::vector<int4> frec;         // per n2t entry: the tet's other three vertices (slot order), code
+    int max_deg = 0, max_nbr = 0;
+};
+
+static void build_adjacency(const int32_t *tets, int64_t n_v, int64_t n_t, int64_t n_real, HostAdjacency &h)
 {
-    // vertex -> (tet*4 + slot), rows sorted
-    std::vector<int> n2t_ptr(n_v + 1, 0);
+    h.n2t_ptr.assign(n_v + 1, 0);
     for (int64_t j = 0; j < n_t; ++j)
         for (int q = 0; q < 4; ++q)
-            if (tets[4 * j + q] < n_real) n2t_ptr[tets[4 * j + q] + 1]++;
-    for (int64_t i = 0; i < n_v; ++i) n2t_ptr[i + 1] += n2t_ptr[i];
-    const int64_t n_faces = n2t_ptr[n_v];
-    std::vector<int> n2t(n_faces > 0 ? n_faces : 1);
+            if (tets[4 * j + q] < n_real) h.n2t_ptr[tets[4 * j + q] + 1]++;
+    for (int64_t i = 0; i < n_v; ++i) h.n2t_ptr[i + 1] += h.n2t_ptr[i];
+    const int64_t n_faces = h.n2t_ptr[n_v];
+    h.n2t.assign(n_faces, 0);
     {
-        std::vector<int> cur(n2t_ptr.begin(), n2t_ptr.end() - 1);
+        std::vector<int> cur(h.n2t_ptr.begin(), h.n2t_ptr.end() - 1);
         for (int64_t j = 0; j < n_t; ++j)
             for (int q = 0; q < 4; ++q)
-                if (tets[4 * j + q] < n_real) n2t[cur[tets[4 * j + q]]++] = (int)(4 * j + q);
+                if (tets[4 * j + q] < n_real) h.n2t[cur[tets[4 * j + q]]++] = (int)(4 * j + q);
     }
-    int max_deg = 0, max_nbr = 0;
-    // vertex -> vertex (neighbours through a shared tet)
-    std::vector<int> n2n_ptr(n_v + 1, 0), n2n;
-    n2n.reserve((size_t)n_t * 3);
+    h.max_deg = h.max_nbr = 0;
+    h.n2n_ptr.assign(n_v + 1, 0);
+    h.n2n.clear();
+    h.n2n.reserve((size_t)n_t * 3);
     std::vector<int> buf;
     for (int64_t i = 0; i < n_v; ++i) {
-        int b = n2t_ptr[i], e = n2t_ptr[i + 1];
-        max_deg = std::max(max_deg, e - b);
+        int b = h.n2t_ptr[i], e = h.n2t_ptr[i + 1];
+        h.max_deg = std::max(h.max_deg, e - b);
         buf.clear();
         for (int p = b; p < e; ++p) {
-            int j = n2t[p] >> 2;
+            int j = h.n2t[p] >> 2;
             for (int q = 0; q < 4; ++q) {
                 int v = tets[4 * (int64_t)j + q];
                 if (v != i && v < n_real) buf.push_back(v);
@@ -398,17 +402,63 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
         }
         std::sort(buf.begin(), buf.end());
         buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-        n2n.insert(n2n.end(), buf.begin(), buf.end());
-        max_nbr = std::max(max_nbr, (int)buf.size());
-        n2n_ptr[i + 1] = (int)n2n.size();
+        h.n2n.insert(h.n2n.end(), buf.begin(), buf.end());
+        h.max_nbr = std::max(h.max_nbr, (int)buf.size());
+        h.n2n_ptr[i + 1] = (int)h.n2n.size();
     }
+    // face records in vertex->tet order: the three other vertices in slot order, code
+    h.frec.resize(n_faces);
+    for (int64_t e = 0; e < n_faces; ++e) {
+        const int code = h.n2t[e];
+        const int64_t j = code >> 2;
+        const int s = code & 3;
+        int f[3], q3 = 0;
+        for (int q = 0; q < 4; ++q)
+            if (q != s) f[q3++] = tets[4 * j + q];
+        h.frec[e] = make_int4(f[0], f[1], f[2], code);
+    }
+}
+
+gbp_status gbp_mesh_adjacency(const int32_t *tets, int64_t n_v, int64_t n_t, int64_t *n_faces, int64_t *n_nbr,
+                              int32_t *n2t_ptr, int32_t *n2t, int32_t *n2n_ptr, int32_t *n2n, int32_t *frec)
+{
+    if (!tets || !n_faces || !n_nbr || n_v < 1 || n_t < 1 || n_v >= (1ll << 30) || n_t >= (1ll << 29))
+        return GBP_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < 4 * n_t; ++k)
+        if (tets[k] < 0 || tets[k] >= n_v) return GBP_ERR_BAD_MESH;
+    HostAdjacency h;
+    build_adjacency(tets, n_v, n_t, n_v, h);
+    *n_faces = (int64_t)h.n2t.size();
+    *n_nbr = (int64_t)h.n2n.size();
+    if (!n2t_ptr || !n2t || !n2n_ptr || !n2n || !frec) return GBP_OK;  // sizes only
+    std::copy(h.n2t_ptr.begin(), h.n2t_ptr.end(), n2t_ptr);
+    std::copy(h.n2t.begin(), h.n2t.end(), n2t);
+    std::copy(h.n2n_ptr.begin(), h.n2n_ptr.end(), n2n_ptr);
+    std::copy(h.n2n.begin(), h.n2n.end(), n2n);
+    for (size_t e = 0; e < h.frec.size(); ++e) {
+        frec[4 * e] = h.frec[e].x;
+        frec[4 * e + 1] = h.frec[e].y;
+        frec[4 * e + 2] = h.frec[e].z;
+        frec[4 * e + 3] = h.frec[e].w;
+    }
+    return GBP_OK;
+}
+
+// Adjacency, face records and device buffers of a validated tet mesh
+// (n_real as in build_adjacency).
+static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const int32_t *tets, int64_t n_t,
+                             int64_t n_real, int dim)
+{
+    HostAdjacency h;
+    build_adjacency(tets, n_v, n_t, n_real, h);
+    const int64_t n_faces = (int64_t)h.n2t.size();
     free_mesh_buffers(c);
     c->n_v = n_v;
     c->n_t = n_t;
     c->n_e = n_real;
     c->dim = dim;
-    c->max_deg = max_deg;
-    c->max_nbr = max_nbr;
+    c->max_deg = h.max_deg;
+    c->max_nbr = h.max_nbr;
     std::vector<float4> x4(n_v);
     for (int64_t i = 0; i < n_v; ++i) x4[i] = make_float4(xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], 0.f);
     cudaError_t err = cudaSuccess;
@@ -421,7 +471,7 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(dalloc(&c->n2t_ptr, n_v + 1));
     CK(dalloc(&c->n2t, n_faces));
     CK(dalloc(&c->n2n_ptr, n_v + 1));
-    CK(dalloc(&c->n2n, (int64_t)n2n.size()));
+    CK(dalloc(&c->n2n, (int64_t)h.n2n.size()));
     CK(dalloc(&c->frec, n_faces));
     CK(dalloc(&c->pc, n_v));
     CK(dalloc(&c->fib, 3 * n_t));
@@ -449,24 +499,11 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(cudaMemset(c->dphi, 0, sizeof(float) * n_v));
     CK(cudaMemcpy(c->xyz, x4.data(), sizeof(float4) * n_v, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(c->tets, tets, sizeof(int4) * n_t, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->n2t_ptr, n2t_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->n2t, n2t.data(), sizeof(int) * n_faces, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->n2n_ptr, n2n_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(c->n2n, n2n.data(), sizeof(int) * n2n.size(), cudaMemcpyHostToDevice));
-    {
-        // face records in vertex->tet order: the three other vertices in slot order, code
-        std::vector<int4> fr(n_faces);
-        for (int64_t e = 0; e < n_faces; ++e) {
-            const int code = n2t[e];
-            const int64_t j = code >> 2;
-            const int s = code & 3;
-            int f[3], q3 = 0;
-            for (int q = 0; q < 4; ++q)
-                if (q != s) f[q3++] = tets[4 * j + q];
-            fr[e] = make_int4(f[0], f[1], f[2], code);
-        }
-        CK(cudaMemcpy(c->frec, fr.data(), sizeof(int4) * fr.size(), cudaMemcpyHostToDevice));
-    }
+    CK(cudaMemcpy(c->n2t_ptr, h.n2t_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2t, h.n2t.data(), sizeof(int) * n_faces, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2n_ptr, h.n2n_ptr.data(), sizeof(int) * (n_v + 1), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->n2n, h.n2n.data(), sizeof(int) * h.n2n.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->frec, h.frec.data(), sizeof(int4) * h.frec.size(), cudaMemcpyHostToDevice));
 #undef CK
     if (err) {
         free_mesh_buffers(c);

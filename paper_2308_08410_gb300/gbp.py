@@ -81,6 +81,7 @@ def load():
         "gbp_upload_mesh_2d": ([P, P, i64, P, i64], i32),
         "gbp_check_mesh": ([P, i64, P, i64], i32),
         "gbp_check_mesh_2d": ([P, i64, P, i64], i32),
+        "gbp_mesh_adjacency": ([P, i64, i64, P, P, P, P, P, P, P], i32),
         "gbp_set_fibres": ([P, P], i32),
         "gbp_set_velocities": ([P, P, P], i32),
         "gbp_set_leadfield": ([P, P, i32], i32),
@@ -131,7 +132,8 @@ def exported_symbols():
     """Names of the entry points this binding expects the library to export."""
     return [
         "gbp_create", "gbp_destroy", "gbp_set_stream", "gbp_status_string", "gbp_synchronize",
-        "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_check_mesh", "gbp_check_mesh_2d", "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
+        "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_check_mesh", "gbp_check_mesh_2d", "gbp_mesh_adjacency",
+        "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
         "gbp_set_onsets", "gbp_set_onsets_batch", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
         "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_forward_backward_batch_host", "gbp_local_solve_batch", "gbp_enable_timing",
@@ -187,6 +189,24 @@ def check_mesh_2d(xy: np.ndarray, tris: np.ndarray) -> int:
     xy = np.ascontiguousarray(xy, np.float32)
     tris = np.ascontiguousarray(tris, np.int32)
     return int(load().gbp_check_mesh_2d(_hptr(xy), xy.shape[0], _hptr(tris), tris.shape[0]))
+
+
+def mesh_adjacency(tets: np.ndarray, n_v: int) -> dict:
+    """The host adjacency the upload builds (gbp_mesh_adjacency): n2t_ptr,
+    n2t (tet * 4 + slot per vertex), n2n_ptr, n2n (neighbours) and frec
+    [n_faces, 4] (the other three vertices in slot order, code)."""
+    tets = np.ascontiguousarray(tets, np.int32)
+    L = load()
+    nf, nn = C.c_int64(0), C.c_int64(0)
+    _check(L.gbp_mesh_adjacency(_hptr(tets), int(n_v), tets.shape[0], C.byref(nf), C.byref(nn),
+                                None, None, None, None, None), "gbp_mesh_adjacency")
+    out = dict(n2t_ptr=np.zeros(n_v + 1, np.int32), n2t=np.zeros(nf.value, np.int32),
+               n2n_ptr=np.zeros(n_v + 1, np.int32), n2n=np.zeros(nn.value, np.int32),
+               frec=np.zeros((nf.value, 4), np.int32))
+    _check(L.gbp_mesh_adjacency(_hptr(tets), int(n_v), tets.shape[0], C.byref(nf), C.byref(nn),
+                                _hptr(out["n2t_ptr"]), _hptr(out["n2t"]), _hptr(out["n2n_ptr"]),
+                                _hptr(out["n2n"]), _hptr(out["frec"])), "gbp_mesh_adjacency")
+    return out
 
 
 def make_opts(local_solver=LOCAL_EXACT, n_f=32, eps=0.0, max_iters=0) -> SolveOpts:

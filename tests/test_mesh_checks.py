@@ -1,8 +1,11 @@
-"""The library's host-side mesh validation (gbp_check_mesh / _2d, the checks
-gbp_upload_mesh and gbp_upload_mesh_2d make before building anything) on
-CPU: valid seeded meshes pass, each kind of defect is refused, and on random
-meshes the verdict equals an independent orientation test in NumPy."""
+"""The library's host-side mesh logic on CPU: the validation the uploads
+make before building anything (gbp_check_mesh / _2d: valid seeded meshes
+pass, each kind of defect is refused, and on random meshes the verdict
+equals an independent orientation test in NumPy) and the adjacency they
+build for the FIM and the adjoint (gbp_mesh_adjacency against a brute-force
+construction)."""
 import numpy as np
+import pytest
 
 from paper_2308_08410_gb300 import gbp
 from paper_2308_08410_gb300 import synth as S
@@ -97,3 +100,55 @@ def test_orientation_verdict_matches_numpy_on_random_meshes():
             cross = np.abs(cross)
         expect = OK if np.all(cross > 0) else BAD
         assert gbp.check_mesh_2d(xy, tris) == expect, trial
+
+
+def brute_adjacency(tets, n_v):
+    """Vertex->tet codes, neighbour sets and face records by definition."""
+    n2t = [[] for _ in range(n_v)]
+    nbr = [set() for _ in range(n_v)]
+    for j, t in enumerate(tets):
+        for q, v in enumerate(t):
+            n2t[v].append(4 * j + q)
+            nbr[v].update(int(u) for u in t if u != v)
+    return n2t, [sorted(s) for s in nbr]
+
+
+def check_adjacency(tets, n_v):
+    a = gbp.mesh_adjacency(tets, n_v)
+    n2t, nbr = brute_adjacency(tets, n_v)
+    assert a["n2t_ptr"][0] == 0 and a["n2n_ptr"][0] == 0
+    assert len(a["n2t"]) == 4 * len(tets)
+    for i in range(n_v):
+        row = a["n2t"][a["n2t_ptr"][i]:a["n2t_ptr"][i + 1]]
+        assert list(row) == sorted(n2t[i]), i
+        assert list(a["n2n"][a["n2n_ptr"][i]:a["n2n_ptr"][i + 1]]) == nbr[i], i
+        for e in range(a["n2t_ptr"][i], a["n2t_ptr"][i + 1]):
+            code = int(a["frec"][e, 3])
+            j, s = code >> 2, code & 3
+            assert code == a["n2t"][e] and tets[j][s] == i
+            assert list(a["frec"][e, :3]) == [int(tets[j][q]) for q in range(4) if q != s]
+
+
+def test_adjacency_matches_its_definition():
+    """The vertex->tet lists (ascending tet * 4 + slot), the neighbour lists
+    (sorted, unique) and the FIM's face records (the other three vertices in
+    slot order) equal a brute-force construction: on a Kuhn cube, on random
+    tets over a few vertex ids (shared faces, isolated vertices) and on a
+    single tet."""
+    m = S.kuhn_cube(4, 10.0)
+    check_adjacency(m.tets, m.n_v)
+    r = np.random.default_rng(3)
+    for _ in range(10):
+        n_v = int(r.integers(5, 40))
+        tets = np.stack([r.choice(n_v, 4, replace=False) for _ in range(int(r.integers(1, 30)))]).astype(np.int32)
+        check_adjacency(tets, n_v)
+    check_adjacency(np.array([[0, 1, 2, 3]], np.int32), 4)
+
+
+def test_adjacency_errors():
+    with pytest.raises(gbp.GbpError) as ei:
+        gbp.mesh_adjacency(np.array([[0, 1, 2, 4]], np.int32), 4)
+    assert ei.value.status == BAD
+    with pytest.raises(gbp.GbpError) as ei:
+        gbp.mesh_adjacency(np.zeros((0, 4), np.int32), 4)
+    assert ei.value.status == INVALID
