@@ -2,9 +2,9 @@
 Algorithm 2) against what the mathematics fixes independently of it:
 planar fronts reproduced exactly by P1 elements, the closed-form point
 source with a constant metric (lower bound + mesh convergence), an
-edge-graph Dijkstra upper bound built with scipy, and order independence of
+edge-graph Dijkstra upper bound built with scipy, order independence of
 the monotone fixed-point iteration (worklist vs. the literal Jacobi sweeps of
-Algorithm 2)."""
+Algorithm 2), and every parent face reproducing its vertex's value."""
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -175,3 +175,38 @@ def test_unreached_component():
     assert np.all(np.isinf(ek["phi"][a.n_v:]))
     assert np.all(ek["parent"][a.n_v:] == O.UNREACHED)
     assert ek["stats"]["unreached"] == b.n_v
+
+
+def test_parent_face_reproduces_phi():
+    """At the fixed point every vertex with a parent face takes that face's
+    local value (Eq. hopflax_local at the minimiser): phi_i equals the
+    alpha-weighted face values plus the metric length of v_i - sum alpha_n v_n
+    in the tet's D, with alpha a point of the simplex, and the face value
+    below phi_i (the paths traced by the parent graph ascend in phi).
+    Heterogeneous fibres and velocities, element onsets; the metric here is
+    built from M = ct^2 I + (cf^2 - ct^2) f f^T independently of the oracle."""
+    p = S.make_c1(n=9, seed=4)
+    r = np.random.default_rng(9)
+    cf = (p.cf * np.exp(0.1 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+    ct = (p.ct * np.exp(0.1 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+    ons = S.onsets_element(p.mesh, 3, seed=5, tmin=0.0, tmax=4.0)
+    ek = O.eikonal(p.mesh, p.fib, cf, ct, ons)
+    xyz = p.mesh.xyz.astype(float)
+    tets = p.mesh.tets
+    checked = 0
+    for i in range(p.mesh.n_v):
+        code = int(ek["parent"][i])
+        if code < 0:
+            continue
+        j, s = code >> 2, code & 3
+        assert tets[j][s] == i
+        face = [int(tets[j][q]) for q in range(4) if q != s]
+        a = ek["alpha"][i]
+        assert np.all(a >= -1e-15) and abs(a.sum() - 1.0) < 1e-12
+        D = np.linalg.inv(conduction_tensor(float(cf[j]), float(ct[j]), p.fib[j].astype(float)))
+        w = xyz[i] - a @ xyz[face]
+        interp = float(a @ ek["phi"][face])
+        assert abs(ek["phi"][i] - (interp + np.sqrt(w @ D @ w))) <= 1e-11 * max(1.0, ek["phi"][i]), i
+        assert interp < ek["phi"][i]
+        checked += 1
+    assert checked > 0.9 * p.mesh.n_v
