@@ -1,7 +1,8 @@
 """Pins of the 2-D oracle (oracle/oracle2d.py): the edge local problem against
 brute-force minimisation, planar fronts reproduced exactly, the point-source
-lower bound with O(h) convergence, and the frozen-graph adjoint against
-central finite differences of the oracle's own loss."""
+lower bound with O(h) convergence, every parent edge reproducing its
+vertex's value, and the frozen-graph adjoint against central finite
+differences of the oracle's own loss."""
 import numpy as np
 import scipy.optimize
 
@@ -164,3 +165,33 @@ def test_element_onset_gradients_vs_finite_differences():
         e[E] = h
         fd = (loss(t, bary, cf + e) - loss(t, bary, cf - e)) / (2 * h)
         assert abs(fd - g["d_cf"][E]) <= 1e-5 * max(abs(fd), 1e-3 * np.abs(g["d_cf"]).max()), (E, fd, g["d_cf"][E])
+
+
+def test_parent_edge_reproduces_phi():
+    """At the fixed point every vertex with a parent edge takes that edge's
+    local value: phi_i equals the alpha-weighted edge values plus the metric
+    length of v_i - sum alpha_n v_n, with the metric M^-1 built here from
+    M = ct^2 I + (cf^2 - ct^2) f f^T (not the oracle's square root), alpha a
+    point of the edge, and the edge value below phi_i."""
+    p = S.make_2d(14, seed=8)
+    mesh = O2.Mesh2D(p.mesh.xy, p.mesh.tris)
+    ek = O2.eikonal(mesh, p.fib, p.cf, p.ct, p.onset_nodes, p.onset_t)
+    checked = 0
+    for i in range(mesh.n_v):
+        code = int(ek["parent"][i])
+        if code < 0:
+            continue
+        j, s = code // 3, code % 3
+        assert mesh.tris[j][s] == i
+        edge = [int(mesh.tris[j][q]) for q in range(3) if q != s]
+        a = ek["alpha"][i]
+        assert np.all(a >= -1e-15) and abs(a.sum() - 1.0) < 1e-12
+        f = np.asarray(p.fib[j], float)
+        f /= np.linalg.norm(f)
+        M = float(p.ct[j]) ** 2 * np.eye(2) + (float(p.cf[j]) ** 2 - float(p.ct[j]) ** 2) * np.outer(f, f)
+        w = mesh.xy[i] - a @ mesh.xy[edge]
+        interp = float(a @ ek["phi"][edge])
+        assert abs(ek["phi"][i] - (interp + np.sqrt(w @ np.linalg.solve(M, w)))) <= 1e-11 * max(1.0, ek["phi"][i])
+        assert interp < ek["phi"][i]
+        checked += 1
+    assert checked > 0.9 * mesh.n_v
