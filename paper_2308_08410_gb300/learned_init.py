@@ -369,8 +369,11 @@ def decode(c5: C5, y: np.ndarray) -> Params:
 
 
 def _closest_bary(tri, p):
-    """Barycentric coordinates of the point of triangle tri closest to p
-    (projection onto the plane, then clamping onto the simplex)."""
+    """Barycentric coordinates of a point of triangle tri near p: those of
+    p's projection onto the triangle's plane, negative ones set to zero and
+    the rest renormalised.  This is the closest point of the triangle when
+    the projection falls inside it; outside it is a point of the triangle's
+    boundary, not necessarily the nearest one."""
     a, b, c = tri
     v0, v1, v2 = b - a, c - a, p - a
     G = np.array([[v0 @ v0, v0 @ v1], [v0 @ v1, v1 @ v1]])
