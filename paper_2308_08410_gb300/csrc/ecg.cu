@@ -120,7 +120,23 @@ static cudaError_t launch_ecg_fwd_leads_b(int N, int ncta, int nb, int threads, 
     return cudaErrorInvalidValue;
 }
 
-// one problem (also used by the allocation-free entry point)
+// The forward kernel for N leads (1..16) as a function pointer, for callers
+// that launch it with cudaLaunchKernel to get that launch's own status;
+// nullptr for other N.
+const void *ecg_fwd_kernel(int N)
+{
+    switch (N) {
+#define GBP_ECG_PTR(n) \
+    case n: return (const void *)k_ecg_fwd_t<n>;
+        GBP_ECG_PTR(1) GBP_ECG_PTR(2) GBP_ECG_PTR(3) GBP_ECG_PTR(4) GBP_ECG_PTR(5) GBP_ECG_PTR(6)
+        GBP_ECG_PTR(7) GBP_ECG_PTR(8) GBP_ECG_PTR(9) GBP_ECG_PTR(10) GBP_ECG_PTR(11) GBP_ECG_PTR(12)
+        GBP_ECG_PTR(13) GBP_ECG_PTR(14) GBP_ECG_PTR(15) GBP_ECG_PTR(16)
+#undef GBP_ECG_PTR
+    }
+    return nullptr;
+}
+
+// one problem
 cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
                                  const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
                                  int64_t per, double *part)

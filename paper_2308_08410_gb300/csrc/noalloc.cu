@@ -14,9 +14,7 @@
 
 namespace gbp {
 // kernels shared with the context-based path (ecg.cu)
-cudaError_t launch_ecg_fwd_leads(int N, int ncta, int threads, size_t smem, cudaStream_t st, int64_t n_v, int T,
-                                 const float *L, const float *phi, float t0, float dt, float c4, int T_tile, int G,
-                                 int64_t per, double *part);
+const void *ecg_fwd_kernel(int N);
 __global__ void k_ecg_reduce(int N, int T, int ncta, const double *__restrict__ part, const float *__restrict__ rowsum,
                              float K0, float dK, float *__restrict__ ecg);
 size_t ecg_fwd_smem(int N, int T_tile, int G);
@@ -71,6 +69,9 @@ __global__ void k_rowsum_noalloc(int64_t n_v, const float *__restrict__ L, float
 
 }  // namespace
 
+// Every launch goes through cudaLaunchKernel, whose return value is that
+// launch's own status: an error left pending by unrelated earlier work on the
+// calling thread is neither reported here nor cleared.
 extern "C" gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t n_v, const float *phi,
                                              const gbp_template *tmpl, float *ecg, void *stream)
 {
@@ -102,12 +103,39 @@ extern "C" gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t
     per = ((per + CH - 1) / CH) * CH;
     ncta = (n_v + per - 1) / per;
     // every partial and row sum is overwritten below, so nothing is cleared
-    k_rowsum_noalloc<<<N, 256, 0, st>>>(n_v, L, rowsum);
-    size_t smem = gbp::ecg_fwd_smem(N, tt, G);
-    if (gbp::launch_ecg_fwd_leads(N, (int)ncta, tt * G, smem, st, n_v, T, L, phi, tmpl->t0, tmpl->dt,
-                                  4.f / tmpl->tau, tt, G, per, part) != cudaSuccess)
-        return GBP_ERR_CUDA;
-    gbp::k_ecg_reduce<<<(N * T + 255) / 256, 256, 0, st>>>(N, T, (int)ncta, part, rowsum, tmpl->K0,
-                                                          tmpl->K1 - tmpl->K0, ecg);
-    return cudaGetLastError() == cudaSuccess ? GBP_OK : GBP_ERR_CUDA;
+    {
+        int64_t nv = n_v;
+        const float *Lp = L;
+        float *rs = rowsum;
+        void *args[] = {&nv, &Lp, &rs};
+        if (cudaLaunchKernel((const void *)k_rowsum_noalloc, dim3(N), dim3(256), args, 0, st) != cudaSuccess)
+            return GBP_ERR_CUDA;
+    }
+    {
+        const void *fn = gbp::ecg_fwd_kernel(N);
+        const size_t smem = gbp::ecg_fwd_smem(N, tt, G);
+        if (!fn || cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return GBP_ERR_CUDA;
+        int64_t nv = n_v, phi_stride = 0, part_stride = 0;
+        int TT = T, T_tile = tt, GG = G;
+        float t0 = tmpl->t0, dt = tmpl->dt, c4 = 4.f / tmpl->tau;
+        const float *Lp = L, *ph = phi;
+        double *pp = part;
+        // k_ecg_fwd_t<N>(n_v, T, L, phi, t0, dt, c4, T_tile, G, per_cta, part, phi_stride, part_stride)
+        void *args[] = {&nv, &TT, &Lp, &ph, &t0, &dt, &c4, &T_tile, &GG, &per, &pp, &phi_stride, &part_stride};
+        if (cudaLaunchKernel(fn, dim3((unsigned)ncta, 1), dim3(tt * G), args, smem, st) != cudaSuccess)
+            return GBP_ERR_CUDA;
+    }
+    {
+        int NN = N, TT = T, nc = (int)ncta;
+        const double *pp = part;
+        const float *rs = rowsum;
+        float K0 = tmpl->K0, dK = tmpl->K1 - tmpl->K0;
+        float *out = ecg;
+        void *args[] = {&NN, &TT, &nc, &pp, &rs, &K0, &dK, &out};
+        if (cudaLaunchKernel((const void *)gbp::k_ecg_reduce, dim3((N * T + 255) / 256), dim3(256), args, 0, st) !=
+            cudaSuccess)
+            return GBP_ERR_CUDA;
+    }
+    return GBP_OK;
 }
