@@ -78,17 +78,38 @@ def run_c2_trajectory(iters=100, lr=1e-2, device=0, log=print):
     V = ctx.ecg_forward(phi_true, p.tmpl).cpu().numpy()
     target = S.add_noise(V, 0.05, 11)
     hist = {}
+    goal = None  # the FP32 arm's final misfit
     for name, prec in (("fp32", gbp.PREC_FP32), ("bf16", gbp.PREC_BF16)):
         inv = InverseProblem(ctx, p, target, precision=prec,
                              init_log_cf=np.full(p.mesh.n_v, np.log(0.6 * 0.8)),
                              init_log_ct=np.full(p.mesh.n_v, np.log(0.3 * 0.8)),
                              init_t=(p.onsets.t + 3.0).astype(np.float32))
-        h, wall = inv.run_adam(iters=iters, lr=lr, log_every=10)
+        arrival = {}
+        t_start = time.perf_counter()
+
+        def check(it, loss, inv=inv, arrival=arrival, t_start=t_start):
+            # the BF16 arm has reached the goal once the FP32 misfit of the same
+            # iterate (its last forward solve) is at or below it
+            if goal is None or arrival or float(loss.item()) > goal:
+                return
+            op = inv.op
+            e32 = ctx.ecg_forward(op.phi, op.tmpl, precision=gbp.PREC_FP32)
+            l32 = float(ctx.ecg_loss_backward(op.phi, e32, op.target, op.tmpl)[0].item())
+            if l32 <= goal:
+                arrival.update(iteration=it, s=time.perf_counter() - t_start, bf16_misfit=float(loss.item()),
+                               fp32_misfit=l32)
+
+        h, wall = inv.run_adam(iters=iters, lr=lr, log_every=10, callback=check if prec == gbp.PREC_BF16 else None)
         # the misfit of the final parameters, always with the FP32 ECG
         inv.op.precision = gbp.PREC_FP32
         final = float(inv.loss().item())
         hist[name] = {"history": h, "final_fp32_misfit": final, "wall_s": wall}
-        log(f"{name}: misfit {h[0][1]:.4g} -> {final:.4g} in {iters} iterations ({wall:.2f} s)")
+        if prec == gbp.PREC_FP32:
+            goal = final
+        else:
+            hist[name]["reached_fp32_goal"] = arrival or None
+        log(f"{name}: misfit {h[0][1]:.4g} -> {final:.4g} in {iters} iterations ({wall:.2f} s)"
+            + (f"; FP32 misfit {goal:.4g} reached at {arrival}" if prec == gbp.PREC_BF16 else ""))
     ctx.close()
     return hist
 

@@ -1,12 +1,19 @@
-"""The learned initialiser end to end at reduced size: data from the forward
-model on the GPU, training with the project's BF16 kernels, and the gain over
-plain Geodesic-BP from the default start on held-out ECGs.
+"""The learned initialiser end to end in the shipped configuration
+(learned_init.run_experiment's defaults, the same call as
+``python -m paper_2308_08410_gb300.learned_init``): 20k training and 2k
+held-out (parameters, ECG) pairs generated by the forward model on the GPU,
+60 epochs of BF16 training with the project's kernels, then on 20 held-out
+noisy ECGs plain Geodesic-BP from the default start (FP32 ECG, 300 Adam
+iterations) against Geodesic-BP from the network's prediction with the BF16
+tensor-core ECG.  Onset relocation across elements is on in both arms, as
+shipped.
 
-At this size (2k training pairs, 12 epochs, 60 refinement iterations) both
-arms keep every onset in its initial tet (no relocation): with relocation the
-plain arm can move its random sites as well, and the small network's gain
-then needs the full-size experiment (python -m
-paper_2308_08410_gb300.learned_init) to show."""
+The learned arm has arrived once the FP32 misfit of its iterate (not its
+BF16 one) is at or below the plain arm's best FP32 misfit, so both arms are
+held to the same error.  The claim tested is the one the method makes for
+the initialiser: its start explains the ECG better than the default start,
+and it reaches the plain method's misfit in less wall time (the median over
+the held-out cases, a case it never reaches counting as never)."""
 import numpy as np
 import pytest
 
@@ -17,13 +24,18 @@ from paper_2308_08410_gb300 import learned_init as LI  # noqa: E402
 pytestmark = pytest.mark.gpu
 
 
-def test_learned_init_beats_default_start():
-    res = LI.run_experiment(n_train=2048, n_test=256, epochs=12, n_eval=6, iters=60, relocate=False,
-                            log=lambda *_: None)
-    m = res["median"]
-    # the network's start already explains the ECG better than the default start
-    assert m["learned_loss0"] < m["plain_loss0"], m
-    # and in most held-out cases it reaches the plain method's best misfit
-    # (over 60 iterations) sooner than the plain method did
-    faster = sum(r["learned_time"] < r["plain_time"] for r in res["cases"])
-    assert faster >= len(res["cases"]) // 2, res["cases"]
+def test_learned_init_beats_default_start_in_the_shipped_configuration():
+    res = LI.run_experiment(log=lambda *_: None)
+    s = LI.summary(res)
+    print(s)
+    assert res["relocate"] and s["cases"] == 20
+    # arrival is judged on the FP32 misfit
+    for r in res["cases"]:
+        if np.isfinite(r["learned_time"]):
+            assert r["learned_fp32_at_arrival"] <= r["plain_best"], r
+    # the network's start explains the ECG better than the default start
+    assert s["median_loss0"]["learned"] < s["median_loss0"]["plain"], s
+    # it reaches the plain method's best misfit in most held-out cases, and
+    # sooner in the median
+    assert s["reached"] >= s["cases"] // 2, s
+    assert s["median_s"]["learned_bf16"] < s["median_s"]["plain_fp32"], s
