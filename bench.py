@@ -34,17 +34,32 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "Geodesic-BP fwd+grad evals/s at 2.15M tets (72^3 Kuhn cube, FP32)"
+METRICS = {
+    "c3": "Geodesic-BP fwd+grad evals/s at 2.15M tets (72^3 Kuhn cube, FP32)",
+    "biv": "Geodesic-BP fwd+grad evals/s on the biventricular shell (FP32)",
+}
+METRIC = METRICS["c3"]
 BATCH = 16                    # default problems per step (multi-start batch)
 BYTES_PER_TET_UPDATE = 92.0   # algorithmic bytes per local face update
 BYTES_PER_ADJ_NODE = 130.0    # algorithmic bytes per vertex of the adjoint
 
 
-def workload_config(n):
+def workload_config(workload, n=72, h=1.0):
+    if workload == "biv":
+        return {
+            "workload": f"c2 biventricular voxel-Kuhn shell, h={h} mm (LV wall 10 mm, RV 4 mm), rule-based "
+                        "fibres -60..+60 deg, c_f/c_t 0.6/0.3 mm/ms with a 1 mm endocardial layer at 2.0 mm/ms, "
+                        "5 element onsets, 12 leads from 10 torso electrodes, T=300 @ 1 ms, misfit vs noisy "
+                        "target; evaluated at synth.c2_starts (tissue velocity scale exp(N(0,0.1)) per start, "
+                        "5 % per-tet log noise, onset times + U(-2,2) ms)",
+            "h": h,
+        }
     return {
         "workload": f"Kuhn cube {n}^3 vertices (10 mm), per-node log c_f/c_t fields -> per-tet "
                     "c (exp of vertex mean), depth-rotating fibres, 10 element onsets, 8 leads "
-                    "(P1 lead field, 1/r kernel, 30 mm sphere), T=150 @ 1 ms, misfit vs noisy target",
+                    "(P1 lead field, 1/r kernel, 30 mm sphere), T=150 @ 1 ms, misfit vs noisy target; "
+                    "evaluated at synth.c3_starts (prior means c_f/c_t 0.6/0.3 x exp(N(0,0.1)) per start, "
+                    "5 % per-vertex log noise, onset times 10 ms (+ U(-2,2) ms))",
         "n": n,
     }
 
@@ -129,10 +144,11 @@ def job_throughput(units_per_rank, world, seconds):
     return world * units_per_rank / seconds
 
 
-def build_inputs(n, seed=0):
+def build_inputs(workload, n=72, h=1.0, seed=0):
     from paper_2308_08410_gb300 import synth as S
-    p = S.make_c3(n=n, seed=seed)
-    return p
+    if workload == "biv":
+        return S.make_c2(h=h, seed=seed)
+    return S.make_c3(n=n, seed=seed)
 
 
 def run_cpu_oracle_eval(p, cf, ct, ons, target):
@@ -142,15 +158,17 @@ def run_cpu_oracle_eval(p, cf, ct, ons, target):
     return time.perf_counter() - t0, r
 
 
-def eval_point(p):
-    """Parameters the benchmark evaluates at: the prior-mean initial guess of
-    the inverse problem (c_f = 0.6, c_t = 0.3 mm/ms, onset times 10 ms at the
-    true sites)."""
+def eval_points(p, B, workload="c3"):
+    """The B starts the benchmark evaluates (synth.c3_starts: the prior-mean
+    velocities with a global scale per start and 5 % per-vertex log noise,
+    onset times 10 ms (+ U(-2, 2) for starts 1..B-1) at the true sites;
+    synth.c2_starts on the biventricular mesh).  Start 0 is the
+    single-evaluation point.  Returns cf, ct [B, n_t], t [B, K] and the onsets
+    of start 0."""
     from paper_2308_08410_gb300 import synth as S
-    cf = np.full(p.mesh.n_t, 0.6, np.float32)
-    ct = np.full(p.mesh.n_t, 0.3, np.float32)
-    ons = S.Onsets(p.onsets.kind, p.onsets.idx, np.full(p.onsets.K, 10.0, np.float32), p.onsets.bary)
-    return cf, ct, ons
+    cf, ct, t = (S.c2_starts if workload == "biv" else S.c3_starts)(p, B)
+    ons0 = S.Onsets(p.onsets.kind, p.onsets.idx, t[0], p.onsets.bary)
+    return cf, ct, t, ons0
 
 
 def main():
@@ -159,7 +177,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["gbp", "reference"], default="gbp")
-    ap.add_argument("--n", type=int, default=72, help="vertices per cube edge")
+    ap.add_argument("--workload", choices=["c3", "biv"], default="c3",
+                    help="c3: 72^3 Kuhn cube (2.15M tets); biv: the biventricular shell (473k tets at h=1 mm)")
+    ap.add_argument("--n", type=int, default=72, help="vertices per cube edge (c3)")
+    ap.add_argument("--h", type=float, default=1.0, help="voxel size in mm (biv)")
     ap.add_argument("--precision", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--local", choices=["exact", "fista"], default="exact")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -186,7 +207,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    p = build_inputs(args.n)
+    p = build_inputs(args.workload, args.n, args.h)
     ctx = gbp.Context(local_rank)
     dp = gbp.setup_problem(ctx, p)
     dev = ctx.torch_device
@@ -196,24 +217,17 @@ def main():
     from paper_2308_08410_gb300 import synth as S
     target_np = S.add_noise(V_true, 0.05, 4242)
     target = torch.from_numpy(target_np).to(dev)
-    cf_np, ct_np, ons = eval_point(p)
+    B = max(1, args.batch)
+    # B starts of the inverse problem (start 0 is also the single-evaluation point)
+    cfB_np, ctB_np, tB_np, ons = eval_points(p, B, args.workload)
+    cf_np, ct_np = cfB_np[0], ctB_np[0]
     cf = torch.from_numpy(cf_np).to(dev)
     ct = torch.from_numpy(ct_np).to(dev)
     t_on = torch.from_numpy(ons.t).to(dev)
     opts = gbp.make_opts(local_solver=gbp.LOCAL_FISTA if args.local == "fista" else gbp.LOCAL_EXACT, n_f=32)
     prec = gbp.PREC_BF16 if args.precision == "bf16" else gbp.PREC_FP32
     out = None
-    B = max(1, args.batch)
     if B > 1:
-        # B starts of the same inverse problem: the prior-mean point with a
-        # global velocity scale exp(N(0, 0.1)) and onset times 10 ms + U(-2, 2)
-        # per start (start 0 is the prior-mean point itself)
-        r = np.random.default_rng(1234)
-        sc_f = np.concatenate([[1.0], np.exp(r.normal(0, 0.1, B - 1))]).astype(np.float32)
-        sc_t = np.concatenate([[1.0], np.exp(r.normal(0, 0.1, B - 1))]).astype(np.float32)
-        cfB_np = np.stack([cf_np * sc_f[b] for b in range(B)])
-        ctB_np = np.stack([ct_np * sc_t[b] for b in range(B)])
-        tB_np = np.stack([ons.t] + [(ons.t + r.uniform(-2, 2, ons.K)).astype(np.float32) for _ in range(B - 1)])
         tgB_np = np.stack([target_np.astype(np.float32)] * B)
         cfB, ctB = torch.from_numpy(cfB_np).to(dev), torch.from_numpy(ctB_np).to(dev)
         tB, tgB = torch.from_numpy(tB_np).to(dev), torch.from_numpy(tgB_np).to(dev)
@@ -346,9 +360,9 @@ def main():
                "sample": "one full evaluation of the same workload (FP64 oracle: worklist Gauss-Seidel "
                          "eikonal single-threaded, ECG / misfit OpenMP, SCC adjoint serial)",
                "seconds": t_cpu, "loss_gpu": float(out["loss"].reshape(-1)[0].item()), "loss_oracle": r["loss"]}
-    traffic = stored_traffic(B, args.n)
+    traffic = stored_traffic(B, args.n) if args.workload == "c3" else None
     line = {
-        "metric": METRIC,
+        "metric": METRICS[args.workload],
         "value": value,
         "unit": "evals/s",
         "n_gpus": world,
@@ -360,8 +374,9 @@ def main():
         "vs_baseline": None,
         "dtype": "f32" if args.precision == "fp32" else "f32 eikonal/adjoint, bf16 ECG",
         "data": "synthetic",
-        "config": dict(workload_config(args.n), n_v=p.mesh.n_v, n_t=p.mesh.n_t, leads=int(p.L.shape[0]),
-                       T=p.tmpl.T, onsets=p.onsets.K, local_solver=args.local, precision=args.precision,
+        "config": dict(workload_config(args.workload, args.n, args.h), n_v=p.mesh.n_v, n_t=p.mesh.n_t,
+                       leads=int(p.L.shape[0]), T=p.tmpl.T, onsets=p.onsets.K, local_solver=args.local,
+                       precision=args.precision,
                        batch=B, l2="flushed between steps (256 MB write)", parallelism="replicas"),
         "tet_updates_per_s": world * face_updates * steps / total_s,
         "fim": {"iterations": st["iterations"], "face_updates": face_updates, "candidates": st["candidates"],
@@ -370,11 +385,15 @@ def main():
                     "cycle_iters": st["adj_cycle_iters"], "ms": adj_ms,
                     "dataflow_ms": st["adj_dataflow_ms"], "cycle_ms": st["adj_cycle_ms"],
                     "roofline": {"bound": "hbm", "achieved": adj_achieved, "peak": peak, "unit": "GB/s",
-                                 "frac": adj_achieved / peak}},
+                                 "frac": adj_achieved / peak,
+                                 "achieved_basis": f"algorithmic bytes: {BYTES_PER_ADJ_NODE:g} B per vertex"}},
         "kernel_ms_per_step": {name: kt_ms[i] / steps for i, name in
                                enumerate(["fim", "parent_pass", "ecg_fwd", "ecg_bwd", "adjoint", "precompute"])},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "k_fim",
+                     "achieved_basis": f"algorithmic bytes: {BYTES_PER_TET_UPDATE:g} B per local face update "
+                                       "(most gathers are served by L2)",
+                     "dram_frac": (traffic / (fim_ms / 1e3) / 1e9 / peak) if traffic else None,
                      "peak_source": peak_kind},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -419,11 +438,12 @@ def run_reference(args, world):
     full evaluation of the same workload (about 12 s); warm-up steps are not
     needed on the CPU and steps stop after ~150 s (the count is reported)."""
     from oracle import oracle as O
-    p = build_inputs(args.n)
+    p = build_inputs(args.workload, args.n, args.h)
     ek = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
     from paper_2308_08410_gb300 import synth as S
     target = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 4242)
-    cf, ct, ons = eval_point(p)
+    cfB, ctB, _, ons = eval_points(p, 1, args.workload)
+    cf, ct = cfB[0], ctB[0]
     times = []
     t_start = time.perf_counter()
     for _ in range(max(1, args.steps)):
@@ -435,7 +455,7 @@ def run_reference(args, world):
     value = len(times) / total
     line = {
         "impl": "reference",
-        "metric": METRIC,
+        "metric": METRICS[args.workload],
         "value": value,
         "unit": "evals/s",
         "n_gpus": world,
@@ -447,8 +467,8 @@ def run_reference(args, world):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": dict(workload_config(args.n), n_v=p.mesh.n_v, n_t=p.mesh.n_t, leads=int(p.L.shape[0]),
-                       T=p.tmpl.T, onsets=p.onsets.K, parallelism="host cores"),
+        "config": dict(workload_config(args.workload, args.n, args.h), n_v=p.mesh.n_v, n_t=p.mesh.n_t,
+                       leads=int(p.L.shape[0]), T=p.tmpl.T, onsets=p.onsets.K, parallelism="host cores"),
         "cpu_baseline": {"value": value, "unit": "evals/s", "cores": O.num_threads(), "kind": "oracle",
                          "sample": f"{len(times)} full evaluations of the workload (steps requested "
                                    f"{args.steps}; capped near 150 s)"},

@@ -492,6 +492,51 @@ def make_c3(n: int = 72, seed: int = 0, side: float = 10.0, n_sites: int = 10,
                           "noise": noise})
 
 
+def c3_starts(p: Problem, B: int, seed: int = 1234, log_noise: float = 0.05):
+    """B starting points of the c3 inverse problem (the multi-start batch the
+    benchmark times): per start a global velocity scale exp(N(0, 0.1)) on the
+    prior means c_f = 0.6 / c_t = 0.3 mm/ms (start 0 unscaled), per-vertex
+    log-velocity noise of std log_noise mapped to tets by the exponential of
+    the vertex mean (the inverse problem's parameterisation), and onset times
+    10 ms (start 0) or 10 ms + U(-2, 2) at the true sites.  The noise keeps
+    exact ties out of the Kuhn cube's faces.  Start b draws from its own
+    generator (seed, b), so a start does not depend on B.  Returns cf, ct
+    float32 [B, n_t] and t float32 [B, K]."""
+    n_v, K = p.mesh.n_v, p.onsets.K
+    cf, ct, t = [], [], []
+    for b in range(B):
+        r = np.random.default_rng([seed, b])
+        sf, st = (1.0, 1.0) if b == 0 else tuple(np.exp(r.normal(0, 0.1, 2)))
+        lcf = np.log(0.6 * sf) + log_noise * r.standard_normal(n_v)
+        lct = np.log(0.3 * st) + log_noise * r.standard_normal(n_v)
+        cf.append(np.exp(nodal_to_tet_mean(p.mesh, lcf)).astype(np.float32))
+        ct.append(np.exp(nodal_to_tet_mean(p.mesh, lct)).astype(np.float32))
+        t.append(np.full(K, 10.0, np.float32) if b == 0 else (10.0 + r.uniform(-2, 2, K)).astype(np.float32))
+    return np.stack(cf), np.stack(ct), np.stack(t)
+
+
+def c2_starts(p: Problem, B: int, seed: int = 4321, log_noise: float = 0.05):
+    """B starting points on the biventricular mesh (the BiV benchmark batch):
+    per start a global scale exp(N(0, 0.1)) on the tissue velocities c_f, c_t
+    (the fast endocardial layer keeps its 2.0 mm/ms), per-tet log-velocity
+    noise of std log_noise on every tet, and the true onset sites with their
+    times (start 0) or those times + U(-2, 2) ms.  Start b draws from its own
+    generator (seed, b).  Returns cf, ct float32 [B, n_t] and t float32
+    [B, K]."""
+    fast = p.extra["fast"]
+    n_t, K = p.mesh.n_t, p.onsets.K
+    cf, ct, t = [], [], []
+    for b in range(B):
+        r = np.random.default_rng([seed, b])
+        sf, st = (1.0, 1.0) if b == 0 else tuple(np.exp(r.normal(0, 0.1, 2)))
+        base_f = np.where(fast, p.cf, p.cf * sf)
+        base_t = np.where(fast, p.ct, p.ct * st)
+        cf.append((base_f * np.exp(log_noise * r.standard_normal(n_t))).astype(np.float32))
+        ct.append((base_t * np.exp(log_noise * r.standard_normal(n_t))).astype(np.float32))
+        t.append(p.onsets.t.astype(np.float32) if b == 0 else (p.onsets.t + r.uniform(-2, 2, K)).astype(np.float32))
+    return np.stack(cf), np.stack(ct), np.stack(t)
+
+
 def make_c4_phi(xyz: np.ndarray, seed: int, tmax: float = 120.0, amp: float = 5.0,
                 n_modes: int = 16) -> np.ndarray:
     """Activation map for the ECG precision study: i.i.d. U[0, tmax] plus a
