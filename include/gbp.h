@@ -224,6 +224,16 @@ gbp_status gbp_set_onsets_batch(gbp_ctx *ctx, int32_t kind, int32_t B, int32_t K
 gbp_status gbp_eikonal_solve(gbp_ctx *ctx, const gbp_solve_opts *opts, float *phi,
                              int32_t *parent, float *alpha);
 
+/* The solution of problem b of the last solve: the activation map phi and
+ * the parent record (Eq. dto_grad's frozen graph).  b = 0 after
+ * gbp_eikonal_solve / gbp_forward_backward, 0 <= b < B after
+ * gbp_forward_backward_batch.  phi float32 [n_v], parent int32 [n_v] and
+ * alpha float32 [n_v][3] (d = 2: [n_v][2]) device pointers in the layouts of
+ * gbp_eikonal_solve; any may be NULL.  Asynchronous.  Errors:
+ * GBP_ERR_INVALID_ARG (b out of range, every output NULL), GBP_ERR_STATE (no
+ * solve recorded since the mesh upload or the last growth of the batch). */
+gbp_status gbp_get_solution(gbp_ctx *ctx, int32_t b, float *phi, int32_t *parent, float *alpha);
+
 /* Synchronises and returns the statistics and status of the last solve and
  * backward pass. */
 gbp_status gbp_get_solve_stats(gbp_ctx *ctx, gbp_solve_stats *stats);
@@ -406,6 +416,19 @@ gbp_status gbp_ecg_forward_noalloc(const float *L, int32_t N, int64_t n_v, const
 gbp_status gbp_local_solve_batch(gbp_ctx *ctx, int64_t n, const float *e, const float *fib,
                                  const float *cf, const float *ct, const float *Phi,
                                  int32_t mode, int32_t n_f, float *value, float *alpha);
+
+/* Failure detection on the device, exercised without a fault: one
+ * cooperative launch of the grid barrier the FIM and the adjoint synchronise
+ * with (one CTA per SM) in which the last absent_ctas CTAs never arrive, so
+ * the other CTAs' bounded waits run out after max_spins polls (a short sleep
+ * each) and latch GBP_ERR_TIMEOUT into the context, exactly as a stalled
+ * solve would.  absent_ctas = 0 is the control case: the barrier completes
+ * and nothing is latched.  The call resets the context's device status
+ * first; the outcome is reported by the next synchronising call
+ * (gbp_synchronize, gbp_get_solve_stats).  The context stays usable: the
+ * next solve resets the status.  Errors: GBP_ERR_INVALID_ARG
+ * (absent_ctas < 0 or >= the SM count, max_spins < 1), GBP_ERR_CUDA. */
+gbp_status gbp_diag_barrier_timeout(gbp_ctx *ctx, int32_t absent_ctas, int32_t max_spins);
 
 /* Kernel timing: when enabled, the library records CUDA events around its
  * main kernels on the context stream.  gbp_get_kernel_times synchronises and

@@ -36,6 +36,13 @@
 // solves mu_c = S_c + a_pc mu_p, mu_p = S_p + a_cp mu_c (S = lambda plus the
 // other children's pushes) and carries on with both.  A pair caught in a
 // longer cycle never becomes ready and goes to the iteration as before.
+//
+// Memory: a hop reads the vertex's 32-byte record written by the parent pass
+// (parent vertices, alpha, the tet and its two velocity coefficients: one
+// sector) and does its atomics: the pushes into the parents' words, which
+// also hold lambda in the same fixed point (so the vertex that completes a
+// parent reads its whole mu from the atomic's return value), and the two
+// gradient additions.  Processed vertices are marked in a bitmap.
 #include "gbp_internal.cuh"
 
 namespace gbp {
@@ -51,7 +58,8 @@ struct AdjArgs {
     const int4 *tets;
     const float4 *tf;  // unit fibre per tet (shared by the batch)
     const float *cf, *ct;
-    const int4 *rec;
+    const int4 *rec;       // (code, alpha bits) per vertex entry: the onset path
+    const int4 *arec;      // the parent pass's 32-byte record per vertex entry
     int onset_kind;
     int site_per_problem;  // on_idx / on_bary hold one site set per problem
     BarGroup *grp;         // group words of the two-level grid barrier
@@ -62,56 +70,60 @@ struct AdjArgs {
     const float *on_bary;
     const float *lam;
     float *mu, *xj, *acc, *acc2;
-    unsigned long long *w;  // packed (child count, fixed-point push sum) per vertex
-    int *proc, *lists;
+    unsigned long long *w;  // packed (child count, fixed-point lambda + push sum) per vertex
+    unsigned int *done;     // processed vertex entries (bitmap)
+    int *lists;
     float *d_cf, *d_ct, *d_t, *d_x;
     Control *ctl;
     int max_cycle_iters;
 };
 
-// m.xyz = unit fibre of the tet
-__device__ __forceinline__ void velocity_terms(float3 w, float4 m, float cfj, float ctj, float mu, float *d_cf,
-                                               float *d_ct, int64_t j)
+// The record of vertex entry v (see the parent pass): parent face vertices
+// f[q] (within the problem, -1 where alpha is 0), alpha a[q], the tet (with
+// the 2-cycle flag in bit 30) or a negative code, and the velocity
+// coefficients.
+constexpr int ADJ_PAIR_FLAG = 1 << 30;
+struct ARec {
+    int f[3];
+    int jt;
+    float a[3];
+    float gcf, gct;
+};
+
+__device__ __forceinline__ ARec load_arec(const int4 *__restrict__ arec, int64_t v)
 {
-    float fw = m.x * w.x + m.y * w.y + m.z * w.z;
-    float3 wp = make_float3(w.x - fw * m.x, w.y - fw * m.y, w.z - fw * m.z);
-    float wp2 = f3dot(wp, wp);
-    float icf = 1.f / cfj, ict = 1.f / ctj;
-    float g = sqrtf(wp2 * ict * ict + fw * fw * icf * icf);
-    if (!(g > 0.f)) return;
-    float ig = 1.f / g;
-    if (d_cf) atomicAdd(&d_cf[j], -mu * fw * fw * icf * icf * icf * ig);
-    if (d_ct) atomicAdd(&d_ct[j], -mu * wp2 * ict * ict * ict * ig);
+    const int4 h = __ldg(&arec[2 * v]);
+    const int4 q = __ldg(&arec[2 * v + 1]);
+    ARec r;
+    r.f[0] = h.x;
+    r.f[1] = h.y;
+    r.f[2] = h.z;
+    r.jt = h.w;
+    r.a[0] = __int_as_float(q.x);
+    r.a[1] = __int_as_float(q.y);
+    r.a[2] = (1.f - r.a[0]) - r.a[1];
+    r.gcf = __int_as_float(q.z);
+    r.gct = __int_as_float(q.w);
+    return r;
+}
+
+// weight of vertex i (within the problem) in the parent face of r (0 if absent)
+__device__ __forceinline__ float face_weight(const ARec &r, int i)
+{
+    return r.f[0] == i ? r.a[0] : r.f[1] == i ? r.a[1] : r.f[2] == i ? r.a[2] : 0.f;
 }
 
 // gradient contributions of vertex i (of problem b) through its own parent
-// (no pushes)
-__device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, int4 r, float m)
+// (no pushes): the tet's velocity terms from the record, or the onset terms
+__device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, const ARec &r, float m)
 {
-    const int code = r.x;
     const int64_t toff = (int64_t)b * a.n_t;
-    if (code >= 0) {
-        const int j = code >> 2, s = code & 3;
-        const int4 tv = __ldg(&a.tets[j]);
-        int ids[4] = {tv.x, tv.y, tv.z, tv.w};
-        const float4 xi = __ldg(&a.xyz[i]);
-        const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-        // w = v_i - sum alpha_n v_n = -sum alpha_n (v_n - v_i)
-        float3 w = make_float3(0.f, 0.f, 0.f);
-        int q3 = 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (q == s) continue;
-            float4 xq = __ldg(&a.xyz[ids[q]]);
-            w.x = fmaf(-al[q3], xq.x - xi.x, w.x);
-            w.y = fmaf(-al[q3], xq.y - xi.y, w.y);
-            w.z = fmaf(-al[q3], xq.z - xi.z, w.z);
-            ++q3;
-        }
-        velocity_terms(w, __ldg(&a.tf[j]), __ldg(&a.cf[toff + j]), __ldg(&a.ct[toff + j]), m, a.d_cf, a.d_ct,
-                       toff + j);
-    } else if (code != GBP_UNREACHED) {
-        const int k = -1 - code;
+    if (r.jt >= 0) {
+        const int64_t j = toff + (r.jt & (ADJ_PAIR_FLAG - 1));
+        if (a.d_cf) atomicAdd(&a.d_cf[j], m * r.gcf);
+        if (a.d_ct) atomicAdd(&a.d_ct[j], m * r.gct);
+    } else if (r.jt != GBP_UNREACHED) {
+        const int k = -1 - r.jt;
         const int bk = b * a.K + k;
         if (a.d_t) atomicAdd(&a.d_t[bk], m);
         if (a.onset_kind == GBP_ONSET_ELEMENT) {
@@ -124,18 +136,19 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, 
             float3 w = make_float3(0.f, 0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                float b = __ldg(&a.on_bary[4 * sk + q]);
+                float bq = __ldg(&a.on_bary[4 * sk + q]);
                 float4 xq = __ldg(&a.xyz[ids[q]]);
-                w.x = fmaf(b, xi.x - xq.x, w.x);
-                w.y = fmaf(b, xi.y - xq.y, w.y);
-                w.z = fmaf(b, xi.z - xq.z, w.z);
+                w.x = fmaf(bq, xi.x - xq.x, w.x);
+                w.y = fmaf(bq, xi.y - xq.y, w.y);
+                w.z = fmaf(bq, xi.z - xq.z, w.z);
             }
             const float4 mm = __ldg(&a.tf[E]);
             const float cfe = __ldg(&a.cf[toff + E]), cte = __ldg(&a.ct[toff + E]);
             float fw = mm.x * w.x + mm.y * w.y + mm.z * w.z;
             float3 wp = make_float3(w.x - fw * mm.x, w.y - fw * mm.y, w.z - fw * mm.z);
+            float wp2 = f3dot(wp, wp);
             float icf = 1.f / cfe, ict = 1.f / cte;
-            float g = sqrtf(f3dot(wp, wp) * ict * ict + fw * fw * icf * icf);
+            float g = sqrtf(wp2 * ict * ict + fw * fw * icf * icf);
             if (g > 0.f) {
                 // D w = wp / ct^2 + (f.w) f / cf^2
                 float ig = 1.f / g;
@@ -145,13 +158,15 @@ __device__ __forceinline__ void local_terms(const AdjArgs &a, int b, int64_t i, 
                     atomicAdd(&a.d_x[3 * bk + 1], -m * (wp.y * c1 + c2 * mm.y) * ig);
                     atomicAdd(&a.d_x[3 * bk + 2], -m * (wp.z * c1 + c2 * mm.z) * ig);
                 }
-                velocity_terms(w, mm, cfe, cte, m, a.d_cf, a.d_ct, toff + E);
+                if (a.d_cf) atomicAdd(&a.d_cf[toff + E], -m * fw * fw * icf * icf * icf * ig);
+                if (a.d_ct) atomicAdd(&a.d_ct[toff + E], -m * wp2 * ict * ict * ict * ig);
             }
         }
     }
 }
 
-// Packed per-vertex word: W = count * 2^55 + S with |S| < 2^54.
+// Packed per-vertex word: W = count * 2^55 + S with |S| < 2^54, S the
+// fixed-point sum of lambda and the pushes received.
 constexpr int ADJ_CNT_SHIFT = 55;
 constexpr unsigned long long ADJ_ONE = 1ull << ADJ_CNT_SHIFT;
 constexpr int ADJ_MAX_CHILDREN = 511;
@@ -166,17 +181,33 @@ __device__ __forceinline__ long long adj_sum(unsigned long long W)
     return (long long)(W - ((unsigned long long)adj_count(W) << ADJ_CNT_SHIFT));
 }
 
-__global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const float *__restrict__ dphi,
-                           unsigned long long *w, int *proc, Control *ctl)
+// fixed-point scale from sum |dL/dphi| (rounded up, so every partial sum of
+// lambda and pushes stays below 2^53 in magnitude)
+__device__ __forceinline__ void adj_scale(const Control *ctl, double *scale, double *iscale)
+{
+    const double lsum = ld_relaxed_f64(&ctl->adj_lsum);
+    const int ex = lsum > 0.0 ? ilogb(lsum) + 1 : 0;
+    *scale = ldexp(1.0, 53 - ex);
+    *iscale = ldexp(1.0, ex - 53);
+}
+
+__device__ __forceinline__ bool is_done(const unsigned int *done, int64_t v)
+{
+    return (__ldcg(&done[v >> 5]) >> (v & 31)) & 1u;
+}
+
+// Zero the words, mark the unreached vertices done and sum |dL/dphi|.  One
+// thread per vertex entry; a warp covers 32 consecutive entries, i.e. one
+// bitmap word.
+__global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ arec, const float *__restrict__ dphi,
+                           unsigned long long *w, unsigned int *done, Control *ctl)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool reached = i < n_v && rec[i].x != GBP_UNREACHED;
+    bool reached = i < n_v && __ldg(&arec[2 * i]).w != GBP_UNREACHED;
     float l = reached ? fabsf(dphi[i]) : 0.f;
-    if (i < n_v) {
-        w[i] = 0ull;
-        proc[i] = reached ? 0 : 1;
-    }
-    // sum |dL/dphi| (bounds every push sum) for the fixed-point scale
+    if (i < n_v) w[i] = 0ull;
+    const unsigned int word = __ballot_sync(0xffffffffu, !reached);
+    if ((threadIdx.x & 31) == 0 && i < n_v) done[i >> 5] = word;
     __shared__ float red[32];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) l += __shfl_xor_sync(0xffffffffu, l, off);
@@ -191,40 +222,22 @@ __global__ void k_adj_init(int64_t n_v, const int4 *__restrict__ rec, const floa
     }
 }
 
-// weight of entry `target` in the parent face recorded in r (0 if absent)
-__device__ __forceinline__ float face_weight(const int4 *__restrict__ tets, int4 r, int boff, int target)
-{
-    if (r.x < 0) return 0.f;
-    const int j = r.x >> 2, s = r.x & 3;
-    const int4 tv = __ldg(&tets[j]);
-    const int f0 = boff + (s == 0 ? tv.y : tv.x), f1 = boff + (s <= 1 ? tv.z : tv.y),
-              f2 = boff + (s <= 2 ? tv.w : tv.z);
-    return target == f0 ? __int_as_float(r.y)
-           : target == f1 ? __int_as_float(r.z)
-           : target == f2 ? __int_as_float(r.w)
-                          : 0.f;
-}
-
 // cand[c] = the parent p of c (weight > 0) whose own parent face holds c
 // (weight > 0), when there is exactly one such parent; else -1
-__global__ void k_adj_cand(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
-                           int *cand)
+__global__ void k_adj_cand(int n_v, int n_tot, const int4 *__restrict__ arec, int *cand)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_tot) return;
-    const int4 r = rec[g];
+    const ARec r = load_arec(arec, g);
     int c = -1, found = 0;
-    if (r.x >= 0) {
+    if (r.jt >= 0) {
         const int boff = (g / n_v) * n_v;
-        const int j = r.x >> 2, s = r.x & 3;
-        const int4 tv = __ldg(&tets[j]);
-        const int f[3] = {boff + (s == 0 ? tv.y : tv.x), boff + (s <= 1 ? tv.z : tv.y), boff + (s <= 2 ? tv.w : tv.z)};
-        const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
-            if (al[q] == 0.f) continue;
-            if (face_weight(tets, rec[f[q]], boff, g) != 0.f) {
-                c = f[q];
+            if (r.f[q] < 0) continue;
+            const ARec rp = load_arec(arec, boff + r.f[q]);
+            if (rp.jt >= 0 && face_weight(rp, g - boff) != 0.f) {
+                c = boff + r.f[q];
                 ++found;
             }
         }
@@ -233,45 +246,47 @@ __global__ void k_adj_cand(int n_v, int n_tot, const int4 *__restrict__ rec, con
 }
 
 // pair[c] = cand[c] when the candidacy is mutual and 1 - a_cp a_pc is not
-// tiny; also clears the pair's hand-over word
-__global__ void k_adj_pair(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
-                           const int *__restrict__ cand, int *pair, unsigned long long *pairw)
+// tiny (the record of c gets the 2-cycle flag); also clears the pair's
+// hand-over word
+__global__ void k_adj_pair(int n_v, int n_tot, int4 *arec, const int *__restrict__ cand, int *pair,
+                           unsigned long long *pairw)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_tot) return;
     int p = cand[g];
     if (p >= 0 && cand[p] == g) {
         const int boff = (g / n_v) * n_v;
-        const float a_gp = face_weight(tets, rec[g], boff, p), a_pg = face_weight(tets, rec[p], boff, g);
+        const ARec rg = load_arec(arec, g), rp = load_arec(arec, p);
+        const float a_gp = face_weight(rg, p - boff), a_pg = face_weight(rp, g - boff);
         if (!(1.f - a_gp * a_pg > 1e-6f)) p = -1;
     } else {
         p = -1;
     }
     pair[g] = p;
     pairw[g] = 0ull;
+    if (p >= 0) arec[2 * (int64_t)g].w |= ADJ_PAIR_FLAG;
 }
 
-__global__ void k_adj_count(int n_v, int n_tot, const int4 *__restrict__ rec, const int4 *__restrict__ tets,
-                            const int *__restrict__ pair, unsigned long long *w)
+// Children per parent word (one ADJ_ONE per face vertex with alpha > 0, the
+// edge to a 2-cycle partner left out) and each vertex's own lambda in the
+// fixed point.
+__global__ void k_adj_count(int n_v, int n_tot, const int4 *__restrict__ arec, const int *__restrict__ pair,
+                            const float *__restrict__ dphi, unsigned long long *w, const Control *ctl)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_tot) return;
-    int4 r = rec[i];
-    if (r.x < 0) return;
+    const ARec r = load_arec(arec, i);
+    if (r.jt == GBP_UNREACHED) return;
+    double scale, iscale;
+    adj_scale(ctl, &scale, &iscale);
+    const long long lf = __double2ll_rn((double)dphi[i] * scale);
+    if (lf) atomicAdd(&w[i], (unsigned long long)lf);
+    if (r.jt < 0) return;
     const int boff = (i / n_v) * n_v;
-    int j = r.x >> 2, s = r.x & 3;
-    int4 tv = tets[j];
-    int ids[4] = {boff + tv.x, boff + tv.y, boff + tv.z, boff + tv.w};
-    int al[3] = {r.y, r.z, r.w};
-    const int partner = pair[i];
-    int q3 = 0;
+    const int partner = (r.jt & ADJ_PAIR_FLAG) ? pair[i] - boff : -1;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (q == s) continue;
-        // the edge to a 2-cycle partner is solved with the pair, not counted
-        if (__int_as_float(al[q3]) != 0.f && ids[q] != partner) atomicAdd(&w[ids[q]], ADJ_ONE);
-        ++q3;
-    }
+    for (int q = 0; q < 3; ++q)
+        if (r.f[q] >= 0 && r.f[q] != partner) atomicAdd(&w[boff + r.f[q]], ADJ_ONE);
 }
 
 // queue slot: vertex id (low word) and mu bits (high word); empty = all ones
@@ -281,11 +296,12 @@ __device__ __forceinline__ unsigned long long adj_item(int v, float m)
 }
 
 // vertices with no children start the dataflow: they go to the work queue
-__global__ void k_adj_seed(int64_t n_v, const unsigned long long *__restrict__ w, const int *__restrict__ proc,
+// (their mu is lambda)
+__global__ void k_adj_seed(int64_t n_v, const unsigned long long *__restrict__ w, const unsigned int *__restrict__ done,
                            const float *__restrict__ dphi, unsigned long long *queue, Control *ctl)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    bool app = i < n_v && proc[i] == 0 && w[i] == 0ull;
+    bool app = i < n_v && !((done[i >> 5] >> (i & 31)) & 1u) && adj_count(w[i]) == 0u;
     unsigned int mask = __ballot_sync(0xffffffffu, app);
     if (mask == 0) return;
     const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
@@ -343,10 +359,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     // per warp), then every busy lane processes one vertex and moves on to
     // the first parent it readied, queueing any further ones.  A warp sleeps
     // only when none of its lanes has work.
-    const double lsum = ld_relaxed_f64(&a.ctl->adj_lsum);
-    // power-of-two scale with sum |dL/dphi| * scale <= 2^53
-    const int ex = lsum > 0.0 ? ilogb(lsum) + 1 : 0;
-    const double scale = ldexp(1.0, 53 - ex), iscale = ldexp(1.0, ex - 53);
+    double scale, iscale;
+    adj_scale(a.ctl, &scale, &iscale);
     unsigned long long *queue = reinterpret_cast<unsigned long long *>(a.lists);
     const int lane = threadIdx.x & 31;
     int v = -1;        // vertex this lane is processing
@@ -393,8 +407,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         if (v >= 0) {
             const int b = v / (int)n_v;
             const int boff = b * (int)n_v;
-            const int4 r = __ldg(&a.rec[v]);
-            const int partner = __ldg(&a.pair[v]);
+            const ARec r = load_arec(a.arec, v);
+            const int partner = (r.jt >= 0 && (r.jt & ADJ_PAIR_FLAG)) ? __ldg(&a.pair[v]) : -1;
             bool go = true;
             if (partner >= 0 && !pre) {
                 // 2-cycle: the first member to be ready leaves its sum in the
@@ -406,8 +420,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                     go = false;
                 } else {
                     const float mq = __uint_as_float((unsigned int)(old & 0xffffffffu));
-                    const float a_vq = face_weight(a.tets, r, boff, partner);              // partner in v's face
-                    const float a_qv = face_weight(a.tets, __ldg(&a.rec[partner]), boff, v);  // v in partner's face
+                    const float a_vq = face_weight(r, partner - boff);                        // partner in v's face
+                    const float a_qv = face_weight(load_arec(a.arec, partner), v - boff);  // v in partner's face
                     const float mv = (m + a_qv * mq) / (1.f - a_vq * a_qv);
                     m = mv;
                     pend[npend++] = adj_item((int)((unsigned int)partner | 0x80000000u), mq + a_vq * mv);
@@ -417,42 +431,33 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
             int next = -1;
             float mnext = 0.f;
             if (go) {
-            a.mu[v] = m;
-            a.proc[v] = 1;
-            ++mine;
-            if (r.x >= 0) {
-                const int j = r.x >> 2, s = r.x & 3;
-                const int4 tv = __ldg(&a.tets[j]);
-                const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-                const int f[3] = {boff + (s == 0 ? tv.y : tv.x), boff + (s <= 1 ? tv.z : tv.y),
-                                  boff + (s <= 2 ? tv.w : tv.z)};
-                unsigned long long nw[3] = {0ull, 0ull, 0ull};
-                float lp[3];
+                atomicOr(&a.done[v >> 5], 1u << (v & 31));
+                ++mine;
+                if (r.jt >= 0) {
+                    unsigned long long nw[3] = {0ull, 0ull, 0ull};
 #pragma unroll
-                for (int q = 0; q < 3; ++q) lp[q] = al[q] != 0.f && f[q] != partner ? __ldg(&a.lam[f[q]]) : 0.f;
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (al[q] == 0.f || f[q] == partner) continue;
-                    const long long c = __double2ll_rn((double)(al[q] * m) * scale);
-                    const unsigned long long d = (unsigned long long)c - ADJ_ONE;
-                    nw[q] = atomicAdd(&a.w[f[q]], d) + d;
-                }
-                local_terms(a, b, v - boff, r, m);
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if (al[q] == 0.f || f[q] == partner || adj_count(nw[q]) != 0u) continue;
-                    // this push completed f[q]: its mu is lambda plus the whole sum
-                    const float mp = lp[q] + (float)((double)adj_sum(nw[q]) * iscale);
-                    if (next < 0) {
-                        next = f[q];
-                        mnext = mp;
-                    } else {
-                        pend[npend++] = adj_item(f[q], mp);
+                    for (int q = 0; q < 3; ++q) {
+                        if (r.f[q] < 0 || boff + r.f[q] == partner) continue;
+                        const long long c = __double2ll_rn((double)(r.a[q] * m) * scale);
+                        const unsigned long long d = (unsigned long long)c - ADJ_ONE;
+                        nw[q] = atomicAdd(&a.w[boff + r.f[q]], d) + d;
                     }
+                    local_terms(a, b, v - boff, r, m);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        if (r.f[q] < 0 || boff + r.f[q] == partner || adj_count(nw[q]) != 0u) continue;
+                        // this push completed the parent: its mu is the whole sum
+                        const float mp = (float)((double)adj_sum(nw[q]) * iscale);
+                        if (next < 0) {
+                            next = boff + r.f[q];
+                            mnext = mp;
+                        } else {
+                            pend[npend++] = adj_item(boff + r.f[q], mp);
+                        }
+                    }
+                } else {
+                    local_terms(a, b, v - boff, r, m);
                 }
-            } else {
-                local_terms(a, b, v - boff, r, m);
-            }
             }
             v = next;
             m = mnext;
@@ -479,8 +484,8 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         }
         // retire the chains that ended.  No fence: their pushes are atomics
         // that have returned, the items they queued were counted before, and
-        // nothing in this loop reads the other writes (mu, proc, gradients),
-        // which the grid barrier after the loop orders.
+        // nothing in this loop reads the other writes (the bitmap, the
+        // gradients), which the grid barrier after the loop orders.
         const unsigned int ends = __ballot_sync(0xffffffffu, ended);
         if (ends) {
             __syncwarp();
@@ -540,10 +545,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     int *R = a.lists + 3 * n_tot;
     for (int64_t base = 0; base < n_tot; base += nth) {
         const int64_t i = base + tid;
-        bool app = i < n_tot && __ldcg(&a.proc[i]) == 0;
+        bool app = i < n_tot && !is_done(a.done, i);
         if (app) {
             // base value: lambda plus the pushes of the processed children
-            const float b0 = __ldg(&a.lam[i]) + (float)((double)adj_sum(__ldcg(&a.w[i])) * iscale);
+            const float b0 = (float)((double)adj_sum(__ldcg(&a.w[i])) * iscale);
             a.mu[i] = b0;
             a.xj[i] = b0;
             a.acc[i] = 0.f;
@@ -562,18 +567,12 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     // (FP32 sums in varying atomic order jitter by about an ulp).
     float *acc_cur = a.acc, *acc_nxt = a.acc2;
     auto push = [&](int i, float x, float *dst) {
-        const int4 r = __ldg(&a.rec[i]);
-        if (r.x < 0) return;
+        const ARec r = load_arec(a.arec, i);
+        if (r.jt < 0) return;
         const int boff = (i / (int)n_v) * (int)n_v;
-        const int j = r.x >> 2, s = r.x & 3;
-        const int4 tv = __ldg(&a.tets[j]);
-        const float al[3] = {__int_as_float(r.y), __int_as_float(r.z), __int_as_float(r.w)};
-        const int f0 = boff + (s == 0 ? tv.y : tv.x);
-        const int f1 = boff + (s <= 1 ? tv.z : tv.y);
-        const int f2 = boff + (s <= 2 ? tv.w : tv.z);
-        if (al[0] != 0.f) atomicAdd(&dst[f0], al[0] * x);
-        if (al[1] != 0.f) atomicAdd(&dst[f1], al[1] * x);
-        if (al[2] != 0.f) atomicAdd(&dst[f2], al[2] * x);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            if (r.f[q] >= 0) atomicAdd(&dst[boff + r.f[q]], r.a[q] * x);
     };
     for (int64_t w = tid; w < nR; w += nth) {
         const int i = __ldcg(&R[w]);
@@ -630,9 +629,9 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         const int i = __ldcg(&R[w]);
         const float x = ld_cg_f(&a.xj[i]);
         a.mu[i] = x;
-        a.proc[i] = 1;
+        atomicOr(&a.done[i >> 5], 1u << (i & 31));
         const int b = i / (int)n_v;
-        local_terms(a, b, i - b * (int)n_v, __ldg(&a.rec[i]), x);
+        local_terms(a, b, i - b * (int)n_v, load_arec(a.arec, i), x);
     }
 }
 
@@ -667,19 +666,18 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     int th = 256;
     unsigned bl = (unsigned)((n_tot + th - 1) / th);
     time_begin(c, 4);
-    k_adj_init<<<bl, th, 0, c->stream>>>(n_tot, c->rec, dphi, c->adj_w, c->proc, c->ctl);
-    k_adj_cand<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_cand);
-    k_adj_pair<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_cand, c->adj_pair,
-                                         c->adj_pairw);
-    k_adj_count<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->rec, c->tets, c->adj_pair, c->adj_w);
-    c->launches += 2;
+    k_adj_init<<<bl, th, 0, c->stream>>>(n_tot, c->adj_rec, dphi, c->adj_w, c->adj_done, c->ctl);
+    k_adj_cand<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->adj_rec, c->adj_cand);
+    k_adj_pair<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->adj_rec, c->adj_cand, c->adj_pair, c->adj_pairw);
+    k_adj_count<<<bl, th, 0, c->stream>>>((int)n_v, (int)n_tot, c->adj_rec, c->adj_pair, dphi, c->adj_w, c->ctl);
+    c->launches += 4;
     if (c->max_nbr > ADJ_MAX_CHILDREN) {
         k_adj_check<<<bl, th, 0, c->stream>>>(n_tot, c->adj_w, c->ctl);
         c->launches++;
     }
-    k_adj_seed<<<bl, th, 0, c->stream>>>(n_tot, c->adj_w, c->proc, dphi,
+    k_adj_seed<<<bl, th, 0, c->stream>>>(n_tot, c->adj_w, c->adj_done, dphi,
                                          reinterpret_cast<unsigned long long *>(c->lists), c->ctl);
-    c->launches += 3;
+    c->launches++;
     if ((err = cudaGetLastError())) return err;
     AdjArgs a;
     a.n_v = n_v;
@@ -692,6 +690,7 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.cf = c->cf;
     a.ct = c->ct;
     a.rec = c->rec;
+    a.arec = c->adj_rec;
     a.onset_kind = c->onset_kind;
     a.site_per_problem = c->site_b > 0;
     a.grp = c->bar_grp;
@@ -703,10 +702,10 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
     a.lam = dphi;
     a.mu = c->mu;
     a.w = c->adj_w;
+    a.done = c->adj_done;
     a.xj = c->jac_x;
     a.acc = c->jac_acc;
     a.acc2 = c->jac_acc2;
-    a.proc = c->proc;
     a.lists = c->lists;
     a.d_cf = d_cf;
     a.d_ct = d_ct;

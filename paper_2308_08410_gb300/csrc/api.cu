@@ -80,7 +80,8 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->adj_cand);
     dfree(&c->adj_pair);
     dfree(&c->adj_pairw);
-    dfree(&c->proc);
+    dfree(&c->adj_rec);
+    dfree(&c->adj_done);
     dfree(&c->L);
     dfree(&c->Lbf);
     dfree(&c->Lscale);
@@ -97,6 +98,7 @@ void free_mesh_buffers(gbp_ctx *c)
     c->N = 0;
     c->K = 0;
     c->solve_gen = -1;
+    c->rec_nb = 0;
 }
 
 gbp_status latched(gbp_ctx *c)
@@ -494,7 +496,8 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(dalloc(&c->adj_cand, n_v));
     CK(dalloc(&c->adj_pair, n_v));
     CK(dalloc(&c->adj_pairw, n_v));
-    CK(dalloc(&c->proc, n_v));
+    CK(dalloc(&c->adj_rec, 2 * n_v));
+    CK(dalloc(&c->adj_done, (n_v + 31) / 32 + 1));
     CK(dalloc(&c->dphi, n_v));
     CK(cudaMemset(c->dphi, 0, sizeof(float) * n_v));
     CK(cudaMemcpy(c->xyz, x4.data(), sizeof(float4) * n_v, cudaMemcpyHostToDevice));
@@ -701,6 +704,7 @@ gbp_status gbp_eikonal_solve(gbp_ctx *c, const gbp_solve_opts *opts, float *phi,
     c->last_mode = o.local_solver;
     c->last_nf = o.n_f;
     c->solve_gen = c->param_gen;
+    c->rec_nb = 1;
     return GBP_OK;
 }
 
@@ -869,6 +873,7 @@ gbp_status gbp_forward_backward_host(gbp_ctx *c, const gbp_solve_opts *opts, con
 // except the first K onset times).
 static cudaError_t ensure_batch(gbp_ctx *c, int B)
 {
+    if (B > c->nb_cap) c->rec_nb = 0;  // the per-problem arrays are rebuilt
     if (B <= c->nb_cap) return cudaSuccess;
     const int64_t nv = c->n_v * B, nt = c->n_t * B;
     cudaError_t err = cudaSuccess;
@@ -895,7 +900,8 @@ static cudaError_t ensure_batch(gbp_ctx *c, int B)
     CK(dalloc(&c->adj_cand, nv));
     CK(dalloc(&c->adj_pair, nv));
     CK(dalloc(&c->adj_pairw, nv));
-    CK(dalloc(&c->proc, nv));
+    CK(dalloc(&c->adj_rec, 2 * nv));
+    CK(dalloc(&c->adj_done, (nv + 31) / 32 + 1));
     CK(dalloc(&c->dphi, nv));
     CK(dalloc(&c->pc, nv));
     if (c->K && !err) {
@@ -973,6 +979,7 @@ gbp_status gbp_forward_backward_batch(gbp_ctx *c, int32_t B, const gbp_solve_opt
     }
     if (!e) e = gbp::launch_fim(c, &o);
     if (!e) e = gbp::launch_parent_pass(c, o.local_solver, o.n_f, nullptr, nullptr, nullptr);
+    c->rec_nb = e ? 0 : B;
     // the ECG and misfit of all B problems in one launch each (the BF16
     // forward still runs problem by problem)
     if (precision == GBP_PREC_BF16) {
@@ -1045,6 +1052,23 @@ gbp_status gbp_local_solve_batch(gbp_ctx *c, int64_t n, const float *e, const fl
     cudaError_t err = cudaMemsetAsync(c->ctl, 0, offsetof(Control, param_status), c->stream);
     if (!err) err = gbp::launch_local_batch(c, n, e, fib, cf, ct, Phi, mode, n_f, value, alpha);
     return from_cuda(err);
+}
+
+gbp_status gbp_get_solution(gbp_ctx *c, int32_t b, float *phi, int32_t *parent, float *alpha)
+{
+    if (!c || (!phi && !parent && !alpha)) return GBP_ERR_INVALID_ARG;
+    if (c->rec_nb < 1) return GBP_ERR_STATE;
+    if (b < 0 || b >= c->rec_nb) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    return from_cuda(gbp::launch_export_solution(c, b, phi, parent, alpha));
+}
+
+gbp_status gbp_diag_barrier_timeout(gbp_ctx *c, int32_t absent_ctas, int32_t max_spins)
+{
+    if (!c || absent_ctas < 0 || max_spins < 1) return GBP_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (absent_ctas >= c->num_sms) return GBP_ERR_INVALID_ARG;
+    return from_cuda(gbp::launch_barrier_probe(c, absent_ctas, (unsigned int)max_spins));
 }
 
 gbp_status gbp_enable_timing(gbp_ctx *c, int32_t on)

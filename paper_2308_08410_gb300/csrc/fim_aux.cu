@@ -225,12 +225,24 @@ cudaError_t launch_unpack_state(gbp_ctx *c)
 // unreached count cover the caller's vertices i < n_e; for a lifted triangle
 // mesh (dim 2) the code is written as triangle * 3 + slot and alpha as the
 // weights of the triangle's two other vertices (the apex weight is 0).
+//
+// It also writes the adjoint's 32-byte record of each vertex entry (two
+// int4), so that one hop of the adjoint reads one sector:
+//   (f0, f1, f2, jt): the parent face's vertices in slot order (within the
+//     problem; -1 where alpha is 0) and the parent tet, or jt = the code for
+//     an onset-held (-1 - k) or unreached vertex (f = -1);
+//   (a0, a1, gcf, gct) as float bits: alpha of f0 and f1 (alpha of f2 is
+//     (1 - a0) - a1, the expression the local solver gives it), and the
+//     derivatives of phi_i = sum alpha_n phi_n + ||w||_D (w = v_i - sum
+//     alpha_n v_n, alpha frozen) with respect to the tet's velocities:
+//     gcf = -(f.w)^2 / (cf^3 ||w||_D), gct = -|w_perp|^2 / (ct^3 ||w||_D).
 template <int MODE>
 __global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t, const float4 *__restrict__ xyz,
                               const int4 *__restrict__ tets, const float4 *__restrict__ tf,
                               const float2 *__restrict__ tv_all, const float4 *__restrict__ tlip_all, int n_f,
-                              const float *__restrict__ phi_all, int4 *rec, float *out_phi, int32_t *out_parent,
-                              float *out_alpha, Control *ctl)
+                              const float *__restrict__ cf_all, const float *__restrict__ ct_all,
+                              const float *__restrict__ phi_all, int4 *rec, int4 *arec, float *out_phi,
+                              int32_t *out_parent, float *out_alpha, Control *ctl)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n_tot) return;
@@ -243,6 +255,8 @@ __global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t,
     int code = r.x;
     float a0 = 0.f, a1 = 0.f, a2 = 0.f;
     float pv = phi_all[i];
+    int4 ar0 = make_int4(-1, -1, -1, code);
+    int4 ar1 = make_int4(0, 0, 0, 0);
     if (code >= 0) {
         int j = code >> 2, s = code & 3;
         int4 tv = tets[j];
@@ -259,13 +273,39 @@ __global__ void k_parent_pass(int n_v, int n_e, int dim, int n_tot, int64_t n_t,
             float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
             lr = local_fista(p, ph, Lv, n_f);
         } else {
-            lr = local_exact(p, ph, &fb);
+            lr = local_exact<true>(p, ph, &fb);
         }
         a0 = lr.a0;
         a1 = lr.a1;
         a2 = lr.a2;
         rec[i] = make_int4(code, __float_as_int(a0), __float_as_int(a1), __float_as_int(a2));
+        // w = v_i - sum alpha_n v_n = -sum alpha_n (v_n - v_i)
+        const float4 xi = xyz[i - b * n_v];
+        const float al[3] = {a0, a1, a2};
+        float3 w = make_float3(0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 xq = xyz[fv[q]];
+            w.x = fmaf(-al[q], xq.x - xi.x, w.x);
+            w.y = fmaf(-al[q], xq.y - xi.y, w.y);
+            w.z = fmaf(-al[q], xq.z - xi.z, w.z);
+        }
+        const float fw = fj.x * w.x + fj.y * w.y + fj.z * w.z;
+        const float3 wp = make_float3(w.x - fw * fj.x, w.y - fw * fj.y, w.z - fw * fj.z);
+        const float wp2 = f3dot(wp, wp);
+        const float icf = 1.f / cf_all[(int64_t)b * n_t + j], ict = 1.f / ct_all[(int64_t)b * n_t + j];
+        const float gg = sqrtf(wp2 * ict * ict + fw * fw * icf * icf);
+        float gcf = 0.f, gct = 0.f;
+        if (gg > 0.f) {
+            const float ig = 1.f / gg;
+            gcf = -fw * fw * icf * icf * icf * ig;
+            gct = -wp2 * ict * ict * ict * ig;
+        }
+        ar0 = make_int4(a0 != 0.f ? fv[0] : -1, a1 != 0.f ? fv[1] : -1, a2 != 0.f ? fv[2] : -1, j);
+        ar1 = make_int4(__float_as_int(a0), __float_as_int(a1), __float_as_int(gcf), __float_as_int(gct));
     }
+    arec[2 * (int64_t)i] = ar0;
+    arec[2 * (int64_t)i + 1] = ar1;
     if (i - b * n_v >= n_e) return;
     if (code == GBP_UNREACHED) atomicAdd(&ctl->unreached, 1ull);
     if (out_phi) out_phi[i] = pv;
@@ -293,13 +333,52 @@ cudaError_t launch_parent_pass(gbp_ctx *c, int mode, int n_f, float *phi, int32_
     time_begin(c, 1);
     if (mode == GBP_LOCAL_FISTA)
         k_parent_pass<GBP_LOCAL_FISTA><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
-                                                                 c->xyz, c->tets, c->tf, c->tv, c->tlip, n_f,
-                                                                 c->phi, c->rec, phi, parent, alpha, c->ctl);
+                                                                 c->xyz, c->tets, c->tf, c->tv, c->tlip, n_f, c->cf,
+                                                                 c->ct, c->phi, c->rec, c->adj_rec, phi, parent,
+                                                                 alpha, c->ctl);
     else
         k_parent_pass<GBP_LOCAL_EXACT><<<bl, th, 0, c->stream>>>((int)c->n_v, (int)c->n_e, c->dim, n_tot, c->n_t,
-                                                                 c->xyz, c->tets, c->tf, c->tv, c->tlip, n_f,
-                                                                 c->phi, c->rec, phi, parent, alpha, c->ctl);
+                                                                 c->xyz, c->tets, c->tf, c->tv, c->tlip, n_f, c->cf,
+                                                                 c->ct, c->phi, c->rec, c->adj_rec, phi, parent,
+                                                                 alpha, c->ctl);
     time_end(c, 1);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// the activation map and parent record of problem b of the last solve, in
+// the caller's layout (the output part of k_parent_pass: codes and alpha for
+// d = 3, triangle codes and two weights for d = 2)
+__global__ void k_export_solution(int n_e, int dim, const float *__restrict__ phi_b, const int4 *__restrict__ rec,
+                                  float *out_phi, int32_t *out_parent, float *out_alpha)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_e) return;
+    if (out_phi) out_phi[i] = phi_b[i];
+    const int4 r = rec[i];
+    const int code = r.x;
+    if (dim == 2) {
+        if (out_parent) out_parent[i] = code >= 0 ? (code >> 2) * 3 + (code & 3) : code;
+        if (out_alpha) {
+            out_alpha[2 * i] = __int_as_float(r.y);
+            out_alpha[2 * i + 1] = __int_as_float(r.z);
+        }
+        return;
+    }
+    if (out_parent) out_parent[i] = code;
+    if (out_alpha) {
+        out_alpha[3 * i] = __int_as_float(r.y);
+        out_alpha[3 * i + 1] = __int_as_float(r.z);
+        out_alpha[3 * i + 2] = __int_as_float(r.w);
+    }
+}
+
+cudaError_t launch_export_solution(gbp_ctx *c, int b, float *phi, int32_t *parent, float *alpha)
+{
+    const int n_e = (int)c->n_e;
+    const int64_t off = (int64_t)b * c->n_v;
+    k_export_solution<<<(n_e + 255) / 256, 256, 0, c->stream>>>(n_e, c->dim, c->phi + off, c->rec + off, phi, parent,
+                                                                  alpha);
     c->launches++;
     return cudaGetLastError();
 }
@@ -329,7 +408,7 @@ __global__ void k_local_batch(int64_t n, const float *__restrict__ e, const floa
     LocalRes r;
     int fb = 0;
     if (mode == GBP_LOCAL_FISTA) r = local_fista(p, ph, face_lipschitz(p), n_f);
-    else r = local_exact(p, ph, &fb);
+    else r = local_exact<true>(p, ph, &fb);
     if (fb) atomicAdd(&ctl->fp64_fallbacks, (unsigned long long)fb);
     value[i] = r.v;
     alpha[3 * i] = r.a0;
@@ -345,6 +424,32 @@ cudaError_t launch_local_batch(gbp_ctx *c, int64_t n, const float *e, const floa
     k_local_batch<<<bl, th, 0, c->stream>>>(n, e, fib, cf, ct, Phi, mode, n_f, value, alpha, c->ctl);
     c->launches++;
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// bounded-wait diagnostic: the grid barrier of the FIM and the adjoint with
+// `absent` CTAs that never arrive, so that every other CTA's wait runs out
+// after max_spins polls and latches GBP_ERR_TIMEOUT (absent = 0: the barrier
+// completes and nothing is latched)
+// ---------------------------------------------------------------------------
+__global__ void k_barrier_probe(Control *ctl, BarGroup *grp, int absent, unsigned int max_spins)
+{
+    if ((int)blockIdx.x >= (int)gridDim.x - absent) return;
+    grid_barrier(ctl, grp, 1u, max_spins);
+}
+
+cudaError_t launch_barrier_probe(gbp_ctx *c, int absent, unsigned int max_spins)
+{
+    cudaError_t err = cudaMemsetAsync(c->ctl, 0, offsetof(Control, param_status), c->stream);
+    if (err) return err;
+    err = cudaMemsetAsync(c->bar_grp, 0, sizeof(BarGroup) * GBP_BAR_GROUPS, c->stream);
+    if (err) return err;
+    Control *ctl = c->ctl;
+    BarGroup *grp = c->bar_grp;
+    void *args[] = {&ctl, &grp, &absent, &max_spins};
+    err = cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3(c->num_sms), dim3(32), args, 0, c->stream);
+    c->launches++;
+    return err;
 }
 
 }  // namespace gbp

@@ -128,6 +128,32 @@ __device__ __forceinline__ float eval_alpha(const float3 p[3], const float ph[3]
     return ref + (s + lsqrt(f3dot(w, w)));
 }
 
+// The objective in FP64 at a boundary candidate, from the FP32 face vectors
+// and values: vertex `kind` (0..2), or edge kind - 3 = 0, 1, 2 for (0, 1),
+// (0, 2), (1, 2) at weight lam on its first vertex and 1 - lam (formed in
+// FP64, so that the weights sum to 1 exactly) on its second.
+__device__ __forceinline__ double eval_candidate64(const float3 p[3], const float ph[3], float ref, int kind, float lam)
+{
+    double a[3] = {0.0, 0.0, 0.0};
+    if (kind < 3) {
+        a[kind] = 1.0;
+    } else {
+        const int e = kind - 3, n = e == 2 ? 1 : 0, m = e == 0 ? 1 : 2;
+        a[n] = lam;
+        a[m] = 1.0 - (double)lam;
+    }
+    double wx = 0.0, wy = 0.0, wz = 0.0, s = 0.0;
+#pragma unroll
+    for (int n = 0; n < 3; ++n) {
+        if (!(a[n] > 0.0)) continue;
+        s += a[n] * ((double)ph[n] - (double)ref);
+        wx += a[n] * p[n].x;
+        wy += a[n] * p[n].y;
+        wz += a[n] * p[n].z;
+    }
+    return (double)ref + (s + sqrt(wx * wx + wy * wy + wz * wz));
+}
+
 #define GBP_TRY(a0_, a1_, a2_)                                   \
     do {                                                         \
         float v_ = eval_alpha(p, ph, ref, (a0_), (a1_), (a2_));  \
@@ -188,6 +214,16 @@ static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0
 // approximate reciprocals (a location error only costs second order in the
 // value); values use IEEE square roots.  p[n] = R (v_{j_n} - v_i),
 // ph[n] = Phi_n (+inf allowed).  fb counts FP64 fallbacks.
+//
+// ALPHA (the parent pass, where the minimiser alpha is an output): the
+// boundary candidates are collected with their FP32 values, and when two or
+// more lie within about 8 ulps of the best, those are re-evaluated in FP64
+// at their (FP32) locations and the smallest FP64 value wins.  Near a
+// vertex, or where two edges meet, candidates a few hundredths apart in
+// alpha differ in value by less than FP32 resolves (a fraction of an ulp),
+// while FP64 separates them; a plain FP32 comparison returns the same value
+// but the other candidate's alpha.
+template <bool ALPHA = false>
 __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float ph[3], int *fb)
 {
     LocalRes r;
@@ -215,8 +251,8 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
         // When 1 - k is too small for FP32, that necessary condition (with
         // a factor-2 and 1e-5 slack for the rounding of k) rules most faces
         // out before the FP64 redo.
-        const float pmax2 = fmaxf(fmaxf(f3dot(p[0], p[0]), f3dot(p[1], p[1])), f3dot(p[2], p[2]));
         const bool near_singular = 1.f - k < GBP_FP64_FALLBACK_TOL;
+        const float pmax2 = fmaxf(fmaxf(f3dot(p[0], p[0]), f3dot(p[1], p[1])), f3dot(p[2], p[2]));
         const bool outside = near_singular && k * S > 2.f * pmax2 * ((1.f - k) + 1e-5f);
         if ((k < 1.f && !outside) || degenerate) {
             float b0, b1;
@@ -238,10 +274,21 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
             }
         }
     }
+    // boundary candidates of the ALPHA variant: FP32 value, kind (vertex n or
+    // edge 3 + e) and edge weight
+    float cv[6], cl[6];
+    int ck[6];
+    int nc = 0;
     // vertices
-    if (ok0) GBP_TRY(1.f, 0.f, 0.f);
-    if (ok1) GBP_TRY(0.f, 1.f, 0.f);
-    if (ok2) GBP_TRY(0.f, 0.f, 1.f);
+    if (ALPHA) {
+        if (ok0) { cv[nc] = eval_alpha(p, ph, ref, 1.f, 0.f, 0.f); ck[nc] = 0; cl[nc] = 1.f; ++nc; }
+        if (ok1) { cv[nc] = eval_alpha(p, ph, ref, 0.f, 1.f, 0.f); ck[nc] = 1; cl[nc] = 1.f; ++nc; }
+        if (ok2) { cv[nc] = eval_alpha(p, ph, ref, 0.f, 0.f, 1.f); ck[nc] = 2; cl[nc] = 1.f; ++nc; }
+    } else {
+        if (ok0) GBP_TRY(1.f, 0.f, 0.f);
+        if (ok1) GBP_TRY(0.f, 1.f, 0.f);
+        if (ok2) GBP_TRY(0.f, 0.f, 1.f);
+    }
     // edges (n, m), lambda = weight on n
 #pragma unroll
     for (int e = 0; e < 3; ++e) {
@@ -262,9 +309,44 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
         float lam = (-dl * h - f3dot(u, p[m])) * iA;
         if (!(lam > 0.f && lam < 1.f)) continue;
         float an = lam, am = 1.f - lam;
+        if (ALPHA) {
+            const float b0 = e == 2 ? 0.f : an, b1 = e == 0 ? am : e == 2 ? an : 0.f, b2 = e == 0 ? 0.f : am;
+            cv[nc] = eval_alpha(p, ph, ref, b0, b1, b2);
+            ck[nc] = 3 + e;
+            cl[nc] = lam;
+            ++nc;
+            continue;
+        }
         if (e == 0) GBP_TRY(an, am, 0.f);
         else if (e == 1) GBP_TRY(an, 0.f, am);
         else GBP_TRY(0.f, an, am);
+    }
+    if (ALPHA && nc > 0) {
+        // the FP32 best, then an FP64 comparison among the near-ties
+        int bq = 0;
+        for (int q = 1; q < nc; ++q)
+            if (cv[q] < cv[bq]) bq = q;
+        const float thr = cv[bq] + 1e-6f * fabsf(cv[bq]);
+        int ties = 0;
+        for (int q = 0; q < nc; ++q) ties += cv[q] <= thr;
+        if (ties > 1) {
+            double best64 = 1e300;
+            for (int q = 0; q < nc; ++q) {
+                if (!(cv[q] <= thr)) continue;
+                const double v64 = eval_candidate64(p, ph, ref, ck[q], cl[q]);
+                if (v64 < best64) {
+                    best64 = v64;
+                    bq = q;
+                }
+            }
+        }
+        // alpha in the solver's own expressions: edge (n, m) at (lam, 1 - lam)
+        const int kq = ck[bq];
+        const float lq = cl[bq], mq = 1.f - lq;
+        r.v = cv[bq];
+        r.a0 = kq == 0 ? 1.f : (kq == 3 || kq == 4) ? lq : 0.f;
+        r.a1 = kq == 1 ? 1.f : kq == 3 ? mq : kq == 5 ? lq : 0.f;
+        r.a2 = kq == 2 ? 1.f : (kq == 4 || kq == 5) ? mq : 0.f;
     }
     return r;
 }
@@ -432,10 +514,10 @@ __device__ __forceinline__ void st_relaxed_u32(unsigned int *p, unsigned int v)
 // lines, so arrivals and polls spread over the groups' lines instead of all
 // CTAs hitting one word.  The last CTA of a group adds one arrival to the grid
 // counter (ctl->barrier); the last group's closes the barrier by releasing
-// every group's word.  The wait is bounded: about 2^22 polls with a short
-// sleep each; on timeout the abort flag and GBP_ERR_TIMEOUT are set and every
-// CTA leaves.  Returns false on abort.  grp: GBP_BAR_GROUPS zeroed entries
-// per launch.
+// every group's word.  The wait is bounded: max_spins polls (2^22 by
+// default) with a short sleep each; on timeout the abort flag and
+// GBP_ERR_TIMEOUT are set and every CTA leaves.  Returns false on abort.
+// grp: GBP_BAR_GROUPS zeroed entries per launch.
 struct BarGroup {
     unsigned int arr;
     unsigned int pad0[31];
@@ -444,7 +526,8 @@ struct BarGroup {
 };
 constexpr unsigned int GBP_BAR_GROUPS = 128;
 
-__device__ __forceinline__ bool grid_barrier(Control *ctl, BarGroup *grp, unsigned int gen)
+__device__ __forceinline__ bool grid_barrier(Control *ctl, BarGroup *grp, unsigned int gen,
+                                             unsigned int max_spins = 1u << 22)
 {
     __shared__ int s_ok2;
     __syncthreads();
@@ -473,7 +556,7 @@ __device__ __forceinline__ bool grid_barrier(Control *ctl, BarGroup *grp, unsign
                 ok = 0;
                 break;
             }
-            if (++spins > (1u << 22)) {
+            if (++spins > max_spins) {
                 atomicExch(&ctl->abort, 1);
                 atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
                 ok = 0;

@@ -67,12 +67,14 @@ struct gbp_ctx {
     gbp::Control *h_ctl = nullptr;  // pinned
     int last_mode = 0, last_nf = 0;
     int64_t param_gen = 0, solve_gen = -1;
+    int rec_nb = 0;  // problems held in the solution (phi, parent record) of the last solve (0: none)
     // adjoint state
     float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;
     unsigned long long *adj_w = nullptr;  // adjoint: packed (child count, push sum) per vertex
     int *adj_cand = nullptr, *adj_pair = nullptr;  // adjoint: 2-cycle candidates and partners per vertex
     unsigned long long *adj_pairw = nullptr;       // adjoint: hand-over word of each 2-cycle (at its smaller entry)
-    int *proc = nullptr;
+    int4 *adj_rec = nullptr;          // adjoint record per vertex entry (two int4, written by the parent pass)
+    unsigned int *adj_done = nullptr;  // adjoint: processed vertex entries, one bit each
     int max_nbr = 0;  // longest vertex->vertex row (bounds a vertex's child count)
     // ECG scratch
     float *ecg_part = nullptr;
@@ -123,6 +125,8 @@ cudaError_t launch_adjoint(gbp_ctx *c, const float *dphi, float *d_cf, float *d_
 cudaError_t launch_local_batch(gbp_ctx *c, int64_t n, const float *e, const float *fib, const float *cf,
                                const float *ct, const float *Phi, int mode, int n_f, float *value,
                                float *alpha);
+cudaError_t launch_barrier_probe(gbp_ctx *c, int absent, unsigned int max_spins);  // fim_aux.cu
+cudaError_t launch_export_solution(gbp_ctx *c, int b, float *phi, int32_t *parent, float *alpha);  // fim_aux.cu
 cudaError_t prepare_leadfield_bf16(gbp_ctx *c);
 // timing: mark the start / end of a kernel class on the context stream
 void flush_timing(gbp_ctx *c);

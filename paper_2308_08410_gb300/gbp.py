@@ -89,6 +89,7 @@ def load():
         "gbp_set_onsets_batch": ([P, i32, i32, i32, P, P, P], i32),
         "gbp_eikonal_solve": ([P, C.POINTER(SolveOpts), P, P, P], i32),
         "gbp_get_solve_stats": ([P, C.POINTER(SolveStats)], i32),
+        "gbp_get_solution": ([P, i32, P, P, P], i32),
         "gbp_ecg_forward": ([P, P, C.POINTER(Template), i32, P], i32),
         "gbp_ecg_loss_backward": ([P, P, P, P, C.POINTER(Template), P, P], i32),
         "gbp_geodesic_backward": ([P, P, P, P, P, P], i32),
@@ -101,6 +102,7 @@ def load():
         "gbp_forward_backward_batch_host": ([P, i32, C.POINTER(SolveOpts), C.POINTER(Template), i32, P, P, P, P,
                                              P, P, P, P, P], i32),
         "gbp_local_solve_batch": ([P, i64, P, P, P, P, P, i32, i32, P, P], i32),
+        "gbp_diag_barrier_timeout": ([P, i32, i32], i32),
         "gbp_enable_timing": ([P, i32], i32),
         "gbp_get_kernel_times": ([P, i32, P, P], i32),
         "gbp_reset_kernel_times": ([P], i32),
@@ -134,9 +136,11 @@ def exported_symbols():
         "gbp_create", "gbp_destroy", "gbp_set_stream", "gbp_status_string", "gbp_synchronize",
         "gbp_upload_mesh", "gbp_upload_mesh_2d", "gbp_check_mesh", "gbp_check_mesh_2d", "gbp_mesh_adjacency",
         "gbp_set_fibres", "gbp_set_velocities", "gbp_set_leadfield",
-        "gbp_set_onsets", "gbp_set_onsets_batch", "gbp_eikonal_solve", "gbp_get_solve_stats", "gbp_ecg_forward",
+        "gbp_set_onsets", "gbp_set_onsets_batch", "gbp_eikonal_solve", "gbp_get_solve_stats",
+        "gbp_get_solution", "gbp_ecg_forward",
         "gbp_ecg_loss_backward", "gbp_geodesic_backward", "gbp_forward_backward",
-        "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_forward_backward_batch_host", "gbp_local_solve_batch", "gbp_enable_timing",
+        "gbp_forward_backward_host", "gbp_forward_backward_batch", "gbp_forward_backward_batch_host", "gbp_local_solve_batch", "gbp_diag_barrier_timeout",
+        "gbp_enable_timing",
         "gbp_get_kernel_times", "gbp_reset_kernel_times", "gbp_launch_count",
         "gbp_ecg_forward_noalloc", "gbp_enable_trace", "gbp_get_trace",
         "gbp_nn_gemm_bf16", "gbp_nn_im2col", "gbp_nn_im2col_t", "gbp_nn_col2im", "gbp_nn_bias_act",
@@ -305,6 +309,17 @@ class Context:
                "gbp_eikonal_solve")
         return phi, parent, alpha
 
+    def solution(self, b: int = 0):
+        """phi [n_v], parent codes [n_v] and alpha [n_v, d] of problem b of
+        the last solve (a batched call keeps all B)."""
+        import torch
+        dev = self.torch_device
+        phi = torch.empty(self.n_v, dtype=torch.float32, device=dev)
+        parent = torch.empty(self.n_v, dtype=torch.int32, device=dev)
+        alpha = torch.empty(self.n_v, self.dim, dtype=torch.float32, device=dev)
+        _check(self.lib.gbp_get_solution(self.h, int(b), _ptr(phi), _ptr(parent), _ptr(alpha)), "gbp_get_solution")
+        return phi, parent, alpha
+
     def stats(self) -> dict:
         s = SolveStats()
         st = self.lib.gbp_get_solve_stats(self.h, C.byref(s))
@@ -427,6 +442,12 @@ class Context:
                                               int(mode), int(n_f), _ptr(val), _ptr(al)),
                "gbp_local_solve_batch")
         return val, al
+
+    def diag_barrier_timeout(self, absent_ctas: int, max_spins: int):
+        """Grid barrier with absent_ctas CTAs that never arrive (bounded
+        waits of max_spins polls); the outcome is latched in the context."""
+        _check(self.lib.gbp_diag_barrier_timeout(self.h, int(absent_ctas), int(max_spins)),
+               "gbp_diag_barrier_timeout")
 
     # ---- timing ---------------------------------------------------------------
     def enable_timing(self, on=True):

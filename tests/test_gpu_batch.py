@@ -1,11 +1,16 @@
 """Batched multi-start evaluation (gbp_forward_backward_batch): every problem
 of the batch against the FP64 oracle and against the single-problem entry
 point, on jittered meshes with different velocities, onset times and
-targets per problem.  Tolerances as in test_gpu_parity.py."""
+targets per problem.  Tolerances as in test_gpu_parity.py
+(parity_helpers.py): each problem's phi, parents and alpha from
+gbp_get_solution, its loss, ECG and gradients (relative L2 1e-3), and its
+per-tet velocity gradients on the tets no tie touched."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
+
+import parity_helpers as PH  # noqa: E402
 
 from oracle import oracle as O  # noqa: E402
 from paper_2308_08410_gb300 import gbp  # noqa: E402
@@ -47,14 +52,34 @@ def batch_problem(n, B, seed, kind="element"):
     return p, cf, ct, t, np.stack(tg)
 
 
+def check_problem(ctx, g, b, p, cf, ct, ons, target, keys):
+    """Problem b of a batched call against the oracle: its solution (phi,
+    parents, alpha), loss, ECG, gradients and per-tet velocity gradients."""
+    ref = O.forward_backward(p.mesh, p.fib, cf, ct, ons, p.L, p.tmpl, target)
+    phi, par, al = (x.cpu().numpy() for x in ctx.solution(b))
+    PH.check_phi(phi, ref)
+    PH.check_parents(par, ref, min_unambiguous=0.9)
+    PH.check_alpha(al, par, p.mesh, p.fib, cf, ct, ref)
+    assert abs(g["loss"][b] - ref["loss"]) / ref["loss"] < 1e-4, (b, g["loss"][b], ref["loss"])
+    assert rel_l2(g["ecg"][b], ref["V"]) < 1e-3
+    # where the GPU took the other face of a tie, the gradient is another
+    # subgradient: a vertex high in the tree moves its adjoint weight to a
+    # neighbouring tet, so the whole vectors are held to 1e-2 there (per tet,
+    # the untouched tets stay at 1e-3 below)
+    tol = 1e-2 if PH.parents_differ(par, ref) else 1e-3
+    for k in keys:
+        assert rel_l2(g[k][b], ref[k]) < tol, (b, k, rel_l2(g[k][b], ref[k]))
+    gb = {"d_cf": g["d_cf"][b], "d_ct": g["d_ct"][b]}
+    PH.check_tet_gradients(gb, ref, par, p.mesh, ons)
+    return ref
+
+
 @pytest.mark.parametrize("kind", ["element", "nodal"])
 def test_batch_matches_oracle_and_single(ctx, kind):
     """Each problem of the batch equals the single-problem entry point on the
     same inputs (the same kernels; the FIM's same-iteration reads make the
     schedule differ, so to rounding) and the oracle at the parity
-    tolerances.  Where the oracle's parent choice is within 1e-5 phi of a
-    tie, the gradient is only a subgradient and the two may split it between
-    different tets, so those problems are held to 1e-2."""
+    tolerances, per tet on the tets no tie touched."""
     B = 3
     p, cf, ct, t, tg = batch_problem(11, B, seed=2, kind=kind)
     gbp.setup_problem(ctx, p)
@@ -62,18 +87,11 @@ def test_batch_matches_oracle_and_single(ctx, kind):
     st = ctx.stats()
     assert st["status"] == 0, st
     g = {k: v.cpu().numpy() for k, v in out.items()}
-    strict = 0
+    keys = ("d_cf", "d_ct", "d_t") + (("d_x",) if kind == "element" else ())
     for b in range(B):
         ons = S.Onsets(p.onsets.kind, p.onsets.idx, t[b], p.onsets.bary)
-        ref = O.forward_backward(p.mesh, p.fib, cf[b], ct[b], ons, p.L, p.tmpl, tg[b])
-        ambiguous = bool(np.any(ref["margin"] <= 1e-5 * np.maximum(1.0, ref["phi"])))
-        tol = 1e-2 if ambiguous else 1e-3
-        strict += not ambiguous
-        assert abs(g["loss"][b] - ref["loss"]) / ref["loss"] < 1e-4, (b, g["loss"][b], ref["loss"])
-        assert rel_l2(g["ecg"][b], ref["V"]) < 1e-3
-        keys = ("d_cf", "d_ct", "d_t") + (("d_x",) if kind == "element" else ())
-        for k in keys:
-            assert rel_l2(g[k][b], ref[k]) < tol, (b, k, rel_l2(g[k][b], ref[k]))
+        check_problem(ctx, g, b, p, cf[b], ct[b], ons, tg[b], keys)
+    for b in range(B):
         # the single-problem entry point on problem b
         ctx.set_onsets(p.onsets.kind, dev(p.onsets.idx, np.int32), dev(t[b]),
                        dev(p.onsets.bary) if p.onsets.bary is not None else None)
@@ -82,7 +100,6 @@ def test_batch_matches_oracle_and_single(ctx, kind):
         for k in keys:
             assert rel_l2(g[k][b], one[k].cpu().numpy()) < 1e-4, (b, k)
         gbp.setup_problem(ctx, p)
-    assert strict >= 1
 
 
 def test_batch_of_one_and_state(ctx):
@@ -139,12 +156,7 @@ def test_batch_with_per_problem_sites(ctx):
     g = {k: v.cpu().numpy() for k, v in out.items()}
     for b in range(B):
         ons = S.Onsets(S.ONSET_ELEMENT, sites[b].idx, t[b], sites[b].bary)
-        ref = O.forward_backward(p.mesh, p.fib, cf[b], ct[b], ons, p.L, p.tmpl, tg[b])
-        ambiguous = bool(np.any(ref["margin"] <= 1e-5 * np.maximum(1.0, ref["phi"])))
-        tol = 1e-2 if ambiguous else 1e-3
-        assert abs(g["loss"][b] - ref["loss"]) / ref["loss"] < 1e-4, b
-        for k in ("d_cf", "d_ct", "d_t", "d_x"):
-            assert rel_l2(g[k][b], ref[k]) < tol, (b, k, rel_l2(g[k][b], ref[k]))
+        check_problem(ctx, g, b, p, cf[b], ct[b], ons, tg[b], ("d_cf", "d_ct", "d_t", "d_x"))
     with pytest.raises(RuntimeError):
         ctx.forward_backward_batch(dev(cf[:2]), dev(ct[:2]), dev(tg[:2]), p.tmpl)
     for b in range(B):

@@ -1,12 +1,16 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle on the
-same seeded inputs.  Tolerances: phi within 1e-4 relative, parents bit-exact
-where the oracle's argmin is unambiguous (margin > 1e-5 phi), ECG within 1e-3
-relative L2, gradients within 1e-3 relative L2."""
+same seeded inputs.  Tolerances (parity_helpers.py states and derives them):
+phi within 2e-6 relative per vertex (the method's bound is 1e-4), parents
+bit-exact where the oracle's argmin is unambiguous (margin > 1e-5 phi),
+alpha within 2e-5 + 4x the oracle's own sensitivity, ECG within 1e-3
+relative L2, gradients within 1e-3 relative L2 and per tet within
+1e-3 |r| + 1e-6 max |r| on the tets no tie touched."""
 import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
 
+import parity_helpers as PH  # noqa: E402
 from oracle import oracle as O  # noqa: E402
 from paper_2308_08410_gb300 import gbp  # noqa: E402
 from paper_2308_08410_gb300 import synth as S  # noqa: E402
@@ -42,18 +46,28 @@ def jittered_c1(n=20, seed=0, kind="element", K=3):
     return p
 
 
-def check_eikonal(ctx, p, opts=None, rtol=1e-4, mode=O.EXACT, n_f=32):
+def check_eikonal(ctx, p, opts=None, eps_stop=False):
+    """phi per vertex, parents where unambiguous and alpha against the oracle.
+    eps_stop: the solve stopped re-activating at decreases <= opts.eps, so
+    phi may sit above the fixed point by eps per hop; then only phi is held,
+    to 1e-4 relative (the method's bound)."""
     gbp.setup_problem(ctx, p)
     phi, parent, alpha = ctx.eikonal_solve(opts)
     st = ctx.stats()
     assert st["status"] == 0, st
-    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, mode=mode, n_f=n_f)
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
     g = phi.cpu().numpy().astype(float)
-    fin = np.isfinite(ref["phi"])
-    np.testing.assert_array_equal(np.isfinite(g), fin)
-    rel = np.abs(g[fin] - ref["phi"][fin]) / np.maximum(1.0, np.abs(ref["phi"][fin]))
-    assert rel.max() < rtol, (rel.max(), st)
-    return g, parent.cpu().numpy(), alpha.cpu().numpy(), ref, st
+    par, al = parent.cpu().numpy(), alpha.cpu().numpy()
+    if eps_stop:
+        fin = np.isfinite(ref["phi"])
+        np.testing.assert_array_equal(np.isfinite(g), fin)
+        rel = np.abs(g[fin] - ref["phi"][fin]) / np.maximum(1.0, ref["phi"][fin])
+        assert rel.max() < 1e-4, rel.max()
+        return g, par, al, ref, st
+    PH.check_phi(g, ref)
+    PH.check_parents(par, ref, min_unambiguous=0.0)
+    PH.check_alpha(al, par, p.mesh, p.fib, p.cf, p.ct, ref)
+    return g, par, al, ref, st
 
 
 # ---------------------------------------------------------------------------
@@ -126,9 +140,7 @@ def test_local_fista(ctx):
 def test_eikonal_c1(ctx):
     p = S.make_c1()
     g, par, al, ref, st = check_eikonal(ctx, p)
-    unamb = ref["margin"] > 1e-5 * np.maximum(1.0, ref["phi"])
-    assert unamb.mean() > 0.9
-    np.testing.assert_array_equal(par[unamb], ref["parent"][unamb])
+    assert PH.unambiguous(ref).mean() > 0.9
     assert st["iterations"] > 5 and st["face_updates"] > p.mesh.n_v
 
 
@@ -148,11 +160,18 @@ def test_eikonal_ragged_sizes(ctx):
     check_eikonal(ctx, p)
 
 
-def test_eikonal_biv(ctx):
+@pytest.mark.parametrize("jitter", [False, True])
+def test_eikonal_biv(ctx, jitter):
+    """The biventricular mesh (h = 1 mm, 95k vertices): phi, every
+    unambiguous parent and alpha; with uniform tissue velocities (where the
+    isotropic fast layer ties edges exactly) and with 5 % velocity jitter."""
     p = S.make_c2()
+    if jitter:
+        r = np.random.default_rng(3)
+        p.cf = (p.cf * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
+        p.ct = (p.ct * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
     g, par, al, ref, st = check_eikonal(ctx, p)
-    unamb = ref["margin"] > 1e-5 * np.maximum(1.0, ref["phi"])
-    assert np.mean(par[unamb] == ref["parent"][unamb]) > 0.999
+    assert PH.unambiguous(ref).mean() > (0.99 if jitter else 0.9)
 
 
 def test_eikonal_eps_and_unreached(ctx):
@@ -165,21 +184,40 @@ def test_eikonal_eps_and_unreached(ctx):
                   np.full(n_t, 0.6, np.float32), np.full(n_t, 0.3, np.float32),
                   S.Onsets(S.ONSET_NODAL, np.array([3], np.int32), np.array([1.0], np.float32)),
                   np.ones((1, mesh.n_v), np.float32), S.Template(T=8))
-    g, par, al, ref, st = check_eikonal(ctx, p, opts=gbp.make_opts(eps=1e-5))
+    g, par, al, ref, st = check_eikonal(ctx, p, opts=gbp.make_opts(eps=1e-5), eps_stop=True)
     assert st["unreached"] == a.n_v
     assert np.all(par[a.n_v:] == gbp.UNREACHED)
 
 
-def test_eikonal_fista_mode(ctx):
-    """Algorithm 1 face values are upper bounds; the FISTA-mode solution lies
-    between the exact fixed point and the exact one plus the FISTA error."""
-    p = S.make_c1(n=14)
+@pytest.mark.parametrize("n_f", [32, 48])
+@pytest.mark.parametrize("jitter", [False, True])
+def test_eikonal_fista_mode(ctx, n_f, jitter):
+    """Algorithm 1 as the local solver of Algorithm 2, vertex by vertex
+    against the oracle's FISTA-mode eikonal at the same n_f in Algorithm 2's
+    own (Jacobi) order.  Algorithm 1 with a fixed n_f is not a monotone
+    function of the face values, so its fixed point depends on the update
+    order (the Gauss-Seidel order lands up to 2e-3 away at n_f = 32, the size
+    of the FISTA error itself); the GPU's iteration reads the previous
+    iteration's values like Algorithm 2 and lands on the Jacobi fixed point
+    to FP32 rounding.  A wrong step, Lipschitz constant or momentum would
+    move it by the FISTA error.  The values also bracket the exact solution
+    from above (Algorithm 1's values are upper bounds)."""
+    if jitter:
+        p = jittered_c1(n=14, seed=3)
+    else:
+        p = S.make_c1(n=14)
     gbp.setup_problem(ctx, p)
-    phi, _, _ = ctx.eikonal_solve(gbp.make_opts(local_solver=gbp.LOCAL_FISTA, n_f=48))
+    phi, _, _ = ctx.eikonal_solve(gbp.make_opts(local_solver=gbp.LOCAL_FISTA, n_f=n_f))
     assert ctx.stats()["status"] == 0
+    g = phi.cpu().numpy().astype(float)
+    ref = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets, mode=O.FISTA, n_f=n_f, order=O.ORDER_JACOBI)
+    rel = np.abs(g - ref["phi"]) / np.maximum(1, ref["phi"])
+    assert rel.max() < 5e-6, rel.max()
     ex = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)["phi"]
-    rel = (phi.cpu().numpy() - ex) / np.maximum(1, ex)
-    assert rel.min() > -2e-6 and rel.max() < 1e-2
+    above = (g - ex) / np.maximum(1, ex)
+    assert above.min() > -2e-6 and above.max() < 1e-2
+    # the FISTA-mode solution is distinguishable from the exact one
+    assert np.median(np.abs(above)) > 10 * np.median(rel)
 
 
 # ---------------------------------------------------------------------------
@@ -215,13 +253,24 @@ def test_ecg_loss_backward(ctx):
 # gradients
 # ---------------------------------------------------------------------------
 
-def gradient_case(ctx, p, precision=gbp.PREC_FP32):
+def gradient_case(ctx, p, precision=gbp.PREC_FP32, per_tet=True):
+    """One forward-plus-gradient evaluation against the oracle; with per_tet,
+    the solution of the same call (phi, parents, alpha) and the per-tet
+    velocity gradients are checked too."""
     dp = gbp.setup_problem(ctx, p)
-    out = ctx.forward_backward(dp.cf, dp.ct, dev(p.extra["target"]), p.tmpl, precision=precision)
+    tgt = p.extra["target"]
+    out = ctx.forward_backward(dp.cf, dp.ct, dev(tgt), p.tmpl, precision=precision)
     st = ctx.stats()
     assert st["status"] == 0, st
-    ref = O.forward_backward(p.mesh, p.fib, p.cf, p.ct, p.onsets, p.L, p.tmpl, p.extra["target"])
-    return {k: v.cpu().numpy() for k, v in out.items()}, ref, st
+    ref = O.forward_backward(p.mesh, p.fib, p.cf, p.ct, p.onsets, p.L, p.tmpl, tgt)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    if per_tet:
+        phi, par, al = (x.cpu().numpy() for x in ctx.solution(0))
+        PH.check_phi(phi, ref)
+        PH.check_parents(par, ref, min_unambiguous=0.9)
+        PH.check_alpha(al, par, p.mesh, p.fib, p.cf, p.ct, ref)
+        g["per_tet"] = PH.check_tet_gradients(g, ref, par, p.mesh, p.onsets)
+    return g, ref, st
 
 
 @pytest.mark.parametrize("kind", ["element", "nodal"])
@@ -262,7 +311,7 @@ def test_gradient_c1_plain(ctx):
     p = S.make_c1()
     ek = O.eikonal(p.mesh, p.fib, (p.cf * 1.07).astype(np.float32), p.ct, p.onsets)
     p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 5)
-    g, ref, st = gradient_case(ctx, p)
+    g, ref, st = gradient_case(ctx, p, per_tet=False)
     assert rel_l2(g["d_t"], ref["d_t"]) < 1e-3
     cen = p.mesh.xyz.astype(float)[p.mesh.tets].mean(axis=1)
     for k in range(4):
@@ -272,9 +321,11 @@ def test_gradient_c1_plain(ctx):
             assert abs(a - b) <= 2e-3 * abs(b) + 1e-3 * np.abs(ref[name]).sum() * 1e-3, (name, a, b)
 
 
-def test_gradient_biv_cycles(ctx):
-    """BiV mesh: the parent graph holds cycles; the adjoint must resolve them."""
-    p = S.make_c2(h=1.6)
+@pytest.mark.parametrize("h", [1.6, 1.0])
+def test_gradient_biv_cycles(ctx, h):
+    """BiV mesh at h = 1.6 and 1 mm (the benchmark's heart-shaped workload):
+    the parent graph holds cycles; the adjoint must resolve them."""
+    p = S.make_c2(h=h)
     r = np.random.default_rng(3)
     # jitter both velocities: the isotropic fast layer otherwise ties exactly
     p.cf = (p.cf * (1 + 0.05 * r.standard_normal(p.mesh.n_t))).astype(np.float32)
