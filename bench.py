@@ -361,6 +361,7 @@ def main():
                          "eikonal single-threaded, ECG / misfit OpenMP, SCC adjoint serial)",
                "seconds": t_cpu, "loss_gpu": float(out["loss"].reshape(-1)[0].item()), "loss_oracle": r["loss"]}
     traffic = stored_traffic(B, args.n) if args.workload == "c3" else None
+    adj_traffic = stored_traffic(B, args.n, kernel="k_adjoint") if args.workload == "c3" else None
     line = {
         "metric": METRICS[args.workload],
         "value": value,
@@ -385,7 +386,10 @@ def main():
                     "cycle_iters": st["adj_cycle_iters"], "ms": adj_ms,
                     "dataflow_ms": st["adj_dataflow_ms"], "cycle_ms": st["adj_cycle_ms"],
                     "roofline": {"bound": "hbm", "achieved": adj_achieved, "peak": peak, "unit": "GB/s",
-                                 "frac": adj_achieved / peak,
+                                 "frac": adj_achieved / peak, "traffic": adj_traffic,
+                                 "traffic_over_algorithmic": (adj_traffic / (B * p.mesh.n_v * BYTES_PER_ADJ_NODE))
+                                 if adj_traffic else None,
+                                 "dram_frac": (adj_traffic / (adj_ms / 1e3) / 1e9 / peak) if adj_traffic else None,
                                  "achieved_basis": f"algorithmic bytes: {BYTES_PER_ADJ_NODE:g} B per vertex"}},
         "kernel_ms_per_step": {name: kt_ms[i] / steps for i, name in
                                enumerate(["fim", "parent_pass", "ecg_fwd", "ecg_bwd", "adjoint", "precompute"])},
@@ -407,28 +411,37 @@ def main():
         dist.destroy_process_group()
 
 
-def kernel_hash() -> str:
-    """Hash of the FIM kernel's sources (the kernel and its device header): a
-    stored ncu traffic figure applies only while it matches."""
+KERNEL_SOURCES = {
+    # the sources a kernel's DRAM traffic depends on (the adjoint reads the
+    # record the parent pass of fim_aux.cu writes)
+    "k_fim": ("fim.cu", "gbp_device.cuh"),
+    "k_adjoint": ("adjoint.cu", "fim_aux.cu", "gbp_device.cuh"),
+}
+TRAFFIC_FILES = {"k_fim": "fim_traffic_c3_batch{batch}.txt", "k_adjoint": "adjoint_traffic_c3_batch{batch}.txt"}
+
+
+def kernel_hash(kernel: str = "k_fim") -> str:
+    """Hash of a kernel's sources: a stored ncu traffic figure applies only
+    while it matches."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("fim.cu", "gbp_device.cuh"):
+    for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
 
 
-def stored_traffic(batch, n, path=None):
-    """DRAM bytes per k_fim launch from the committed ncu summary for this
-    workload, or None when there is none or it was taken on other kernel
+def stored_traffic(batch, n, path=None, kernel: str = "k_fim"):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary for
+    this workload, or None when there is none or it was taken on other kernel
     sources (its kernel_hash differs), another batch size or mesh."""
-    path = path or os.path.join(ROOT, "profiles", f"fim_traffic_c3_batch{batch}.txt")
+    path = path or os.path.join(ROOT, "profiles", TRAFFIC_FILES[kernel].format(batch=batch))
     try:
         with open(path) as f:
             tj = json.load(f)
     except (OSError, ValueError):
         return None
-    if tj.get("kernel_hash") == kernel_hash() and tj.get("batch") == batch and tj.get("n") == n:
+    if tj.get("kernel_hash") == kernel_hash(kernel) and tj.get("batch") == batch and tj.get("n") == n:
         return tj.get("bytes_per_launch")
     return None
 
