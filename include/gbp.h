@@ -90,6 +90,8 @@ typedef struct {
     int32_t reserved;
     double adj_dataflow_ms; /* adjoint: device time of the dataflow phase */
     double adj_cycle_ms;    /* adjoint: device time of the cycle iteration */
+    int64_t fim_deferred;   /* faces the FIM left to the FP64 repair (their interior step needs FP64) */
+    int64_t fim_repaired;   /* vertices the repair lowered (the exact iteration resumed from them) */
 } gbp_solve_stats;
 
 /* Template action potential (Eq. tanh_waveform), read as

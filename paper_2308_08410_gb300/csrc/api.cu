@@ -81,6 +81,7 @@ void free_mesh_buffers(gbp_ctx *c)
     dfree(&c->adj_pair);
     dfree(&c->adj_pairw);
     dfree(&c->adj_rec);
+    dfree(&c->defer);
     dfree(&c->adj_done);
     dfree(&c->L);
     dfree(&c->Lbf);
@@ -497,6 +498,7 @@ static gbp_status build_mesh(gbp_ctx *c, const float *xyz, int64_t n_v, const in
     CK(dalloc(&c->adj_pair, n_v));
     CK(dalloc(&c->adj_pairw, n_v));
     CK(dalloc(&c->adj_rec, 2 * n_v));
+    CK(dalloc(&c->defer, gbp::FIM_DEFER_CAP));
     CK(dalloc(&c->adj_done, (n_v + 31) / 32 + 1));
     CK(dalloc(&c->dphi, n_v));
     CK(cudaMemset(c->dphi, 0, sizeof(float) * n_v));
@@ -727,6 +729,8 @@ gbp_status gbp_get_solve_stats(gbp_ctx *c, gbp_solve_stats *s)
     s->reserved = 0;
     s->adj_dataflow_ms = h.adj_ts[1] > h.adj_ts[0] ? (double)(h.adj_ts[1] - h.adj_ts[0]) * 1e-6 : 0.0;
     s->adj_cycle_ms = h.adj_ts[2] > h.adj_ts[1] ? (double)(h.adj_ts[2] - h.adj_ts[1]) * 1e-6 : 0.0;
+    s->fim_deferred = h.n_defer;
+    s->fim_repaired = h.n_repaired;
     return (gbp_status)s->status;
 }
 

@@ -33,6 +33,8 @@ struct FimArgs {
     int max_iters;
     int n_f;
     long long *trace;  // optional: per iteration (active vertices, global timer ns)
+    int2 *defer;       // faces deferred to the FP64 repair (DEFER kernels): (vertex entry, face record)
+    int resume;        // continue from the state and list the repair left (iteration numbers go on)
 };
 
 // One iteration k = one Jacobi-style sweep of Algorithm 2 restricted to the
@@ -51,14 +53,10 @@ struct FimArgs {
 #ifndef GBP_FIM_G
 #define GBP_FIM_G 8  // lanes per active vertex
 #endif
-#ifndef GBP_FIM_R
-#define GBP_FIM_R 1  // faces per lane fetched together
-#endif
 #ifndef GBP_FIM_BLOCK
 #define GBP_FIM_BLOCK 1024  // threads per CTA
 #endif
 constexpr int FIM_G = GBP_FIM_G;
-constexpr int FIM_R = GBP_FIM_R;
 constexpr int FIM_BLOCK = GBP_FIM_BLOCK;
 // One CTA of 1024 threads per SM (64 registers): the same 32 warps per SM as
 // four CTAs of 256, with a quarter of the grid barrier's arrivals and each
@@ -79,93 +77,89 @@ constexpr int FIM_CAP = GBP_FIM_CAP;
 // One active vertex (entry g of the list) handled by a group of G lanes:
 // its faces in rounds of G, the (value, code) minimum over the group, the
 // update of its state and the activation of its neighbours for k + 1.
-template <int MODE, int G>
-__device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int64_t g, bool act, const int *__restrict__ list,
+// Register budget (64 at 32 warps per SM): only what the face loop needs is
+// held across it; the vertex's own position is re-read per face (an L1
+// hit), its own value and change stamp and its neighbour range after the
+// loop, so that the solver's working set stays in registers (every value
+// held across the loop was otherwise spilled to local memory, whose
+// traffic through L1/L2 exceeded the kernel's DRAM traffic).
+//
+// DEFER: the exact solver does not take its rare FP64 interior step here; such
+// a face contributes its boundary minimum (an upper bound of its value) and
+// is recorded for the repair after the solve (launch_fim), which re-solves it
+// in full and resumes the iteration from any vertex it lowers.  Any FP64 code
+// in this kernel made the register allocator spill the face loop's state
+// (measured: 9 % of the kernel's time).
+template <int MODE, bool DEFER, int G>
+__device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int g, bool act, const int *__restrict__ list,
                                            int *nlist, int nxt, int *s_list, int *s_n, int &fb_local,
                                            unsigned int &my_faces)
 {
-    const int64_t n_v = a.n_v;
+    const int n_v = (int)a.n_v;
     const int sub = threadIdx.x & (G - 1);
     // entry gi = b * n_v + i: vertex i of problem b
-    int gi = 0, i = 0, boff = 0, beg = 0, end = 0, nb = 0, ne = 0, chg_old = 0;
-    int64_t toff = 0;
-    float phi_old = 0.f;
-    float4 xi = make_float4(0.f, 0.f, 0.f, 0.f);
+    int gi = 0, boff = 0, toff = 0, beg = 0, end = 0;
     if (act) {
         gi = __ldcg(&list[g]);
-        const int b = gi / (int)n_v;
-        boff = b * (int)n_v;
-        toff = (int64_t)b * a.n_t;
-        i = gi - boff;
-        const int2 own = FIM_LD(&a.pc[gi]);
-        phi_old = __int_as_float(own.x);
-        chg_old = own.y;
-        beg = __ldg(&a.n2t_ptr[i]);
-        end = __ldg(&a.n2t_ptr[i + 1]);
-        nb = __ldg(&a.n2n_ptr[i]);
-        ne = __ldg(&a.n2n_ptr[i + 1]);
-        xi = __ldg(&a.xyz[i]);
+        const int b = gi / n_v;
+        boff = b * n_v;
+        toff = b * (int)a.n_t;  // b * n_t < 2^31 (checked at set-up)
+        beg = __ldg(&a.n2t_ptr[gi - boff]);
+        end = __ldg(&a.n2t_ptr[gi - boff + 1]);
     }
     const int maxdeg = __reduce_max_sync(0xffffffffu, end - beg);
     float best = GBP_INF;
     int best_code = 0x7fffffff;
-    // FIM_R faces per lane at a time: their adjacency, tets and face
-    // values are fetched together (three dependent loads for all of
-    // them), then the masked ones are solved
-    for (int e0 = 0; e0 < maxdeg; e0 += G * FIM_R) {
-        // the face record (face vertex ids, code), then each face
-        // vertex's packed value and change stamp
-        int4 fr[FIM_R];
-#pragma unroll
-        for (int r = 0; r < FIM_R; ++r) {
-            const int e = beg + e0 + r * G + sub;
-            fr[r] = e < end ? __ldg(&a.frec[e]) : make_int4(0, 0, 0, -1);
-        }
+    for (int e0 = 0; e0 < maxdeg; e0 += G) {
+        // the face record (face vertex ids, code), then each face vertex's
+        // packed value and change stamp
+        const int e = beg + e0 + sub;
+        const int4 fr = e < end ? __ldg(&a.frec[e]) : make_int4(0, 0, 0, -1);
         // the face's per-problem velocity terms (the one input of the solve
         // that is mostly not in L2 once a batch is in flight) depend only on
         // the face record: issued before the face values come back
-        float2 vj[FIM_R];
-#pragma unroll
-        for (int r = 0; r < FIM_R; ++r)
-            if (fr[r].w >= 0) vj[r] = __ldg(&a.tv[toff + (fr[r].w >> 2)]);
-        float ph[FIM_R][3];
-        bool mk[FIM_R];
-#pragma unroll
-        for (int r = 0; r < FIM_R; ++r) {
-            mk[r] = false;
-            ph[r][0] = ph[r][1] = ph[r][2] = GBP_INF;
-            if (fr[r].w >= 0) {
-                const int2 q0 = FIM_LD(&a.pc[boff + fr[r].x]), q1 = FIM_LD(&a.pc[boff + fr[r].y]),
-                           q2 = FIM_LD(&a.pc[boff + fr[r].z]);
-                ph[r][0] = __int_as_float(q0.x);
-                ph[r][1] = __int_as_float(q1.x);
-                ph[r][2] = __int_as_float(q2.x);
-                mk[r] = max(q0.y, max(q1.y, q2.y)) >= k - 1;
-            }
+        float2 vj = make_float2(0.f, 0.f);
+        if (fr.w >= 0) vj = __ldg(&a.tv[toff + (fr.w >> 2)]);
+        float ph[3] = {GBP_INF, GBP_INF, GBP_INF};
+        bool mk = false;
+        if (fr.w >= 0) {
+            const int2 q0 = FIM_LD(&a.pc[boff + fr.x]), q1 = FIM_LD(&a.pc[boff + fr.y]),
+                       q2 = FIM_LD(&a.pc[boff + fr.z]);
+            ph[0] = __int_as_float(q0.x);
+            ph[1] = __int_as_float(q1.x);
+            ph[2] = __int_as_float(q2.x);
+            mk = max(q0.y, max(q1.y, q2.y)) >= k - 1;
         }
-#pragma unroll
-        for (int r = 0; r < FIM_R; ++r) {
-            if (!mk[r]) continue;
-            const int code_r = fr[r].w;
-            const int j = code_r >> 2, s = code_r & 3;
+        if (mk) {
+            const int code_r = fr.w;
+            const int j = code_r >> 2;
             ++my_faces;
             // metric: the fibre shared by the batch, the velocity terms of this problem
             const float4 fj = __ldg(&a.tf[j]);
-            const float4 m = make_float4(fj.x, fj.y, fj.z, vj[r].x);
-            const float sd = vj[r].y;
-            const float4 x0 = __ldg(&a.xyz[fr[r].x]), x1 = __ldg(&a.xyz[fr[r].y]),
-                         x2 = __ldg(&a.xyz[fr[r].z]);
+            const float4 m = make_float4(fj.x, fj.y, fj.z, vj.x);
+            const float sd = vj.y;
+            const float4 xi = __ldg(&a.xyz[gi - boff]);
+            const float4 x0 = __ldg(&a.xyz[fr.x]), x1 = __ldg(&a.xyz[fr.y]), x2 = __ldg(&a.xyz[fr.z]);
             float3 p[3];
             p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, sd);
             p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, sd);
             p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, sd);
             LocalRes res;
             if (MODE == GBP_LOCAL_FISTA) {
+                const int s = code_r & 3;
                 const float4 Lq = __ldg(&a.tlip[toff + j]);
                 const float Lv = s == 0 ? Lq.x : s == 1 ? Lq.y : s == 2 ? Lq.z : Lq.w;
-                res = local_fista(p, ph[r], Lv, a.n_f);
+                res = local_fista(p, ph, Lv, a.n_f);
+            } else if (DEFER) {
+                bool need64 = false;
+                res = local_exact<false, true>(p, ph, &fb_local, &need64);
+                if (need64) {
+                    const int pos = atomicAdd(&a.ctl->n_defer, 1);
+                    if (pos < FIM_DEFER_CAP) a.defer[pos] = make_int2(gi, e);
+                    else atomicExch(&a.ctl->defer_overflow, 1);
+                }
             } else {
-                res = local_exact(p, ph[r], &fb_local);
+                res = local_exact(p, ph, &fb_local);
             }
             if (res.v < best || (res.v == best && code_r < best_code)) {
                 best = res.v;
@@ -183,17 +177,27 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int64_t g, b
             best_code = oc;
         }
     }
+    // the vertex's own value and change stamp: only this group writes them in
+    // this iteration, so the value read now is the one the iteration began with
     bool changed = false;
-    if (act && best < phi_old) {
-        changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
-        if (sub == 0) {
-            // value and change stamp in one 8-byte store: readers see a pair
-            a.pc[gi] = make_int2(__float_as_int(best), changed ? k : chg_old);
-            a.rec[gi].x = best_code;
+    int nb = 0, ne = 0;
+    if (act) {
+        const int2 own = FIM_LD(&a.pc[gi]);
+        const float phi_old = __int_as_float(own.x);
+        if (best < phi_old) {
+            changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
+            if (sub == 0) {
+                // value and change stamp in one 8-byte store: readers see a pair
+                a.pc[gi] = make_int2(__float_as_int(best), changed ? k : own.y);
+                a.rec[gi].x = best_code;
+            }
+        }
+        if (changed) {
+            nb = __ldg(&a.n2n_ptr[gi - boff]);
+            ne = __ldg(&a.n2n_ptr[gi - boff + 1]);
         }
     }
     // activate the neighbours of changed vertices for iteration k+1
-    if (!changed) nb = ne = 0;
     const int maxn = __reduce_max_sync(0xffffffffu, ne - nb);
     for (int e0 = 0; e0 < maxn; e0 += G) {
         const int e = nb + e0 + sub;
@@ -211,15 +215,19 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int64_t g, b
     }
 }
 
-template <int MODE>
+// The persistent FIM.  DEFER (the exact solver's main solve) leaves the
+// faces that need the FP64 interior step to the repair below; resume (the
+// exact solver without DEFER, after the repair) continues the iteration from
+// the list the repair built, numbering iterations on from the main solve.
+template <int MODE, bool DEFER>
 __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
 {
     const int lane = threadIdx.x & 31;
     const int groups_per_block = blockDim.x / FIM_G;
-    const int64_t ggroup = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / FIM_G;
-    const int64_t ngroups = (int64_t)gridDim.x * groups_per_block;
-    const int64_t gwarp = (int64_t)blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
-    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int ggroup = blockIdx.x * groups_per_block + threadIdx.x / FIM_G;
+    const int ngroups = gridDim.x * groups_per_block;
+    const int gwarp = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    const int nwarps = gridDim.x * (blockDim.x / 32);
     __shared__ int s_list[FIM_CAP];
     __shared__ int s_n, s_cnt, s_base;
     __shared__ unsigned long long s_cand, s_faces;
@@ -232,10 +240,14 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
     }
     __syncthreads();
     unsigned int nbar = 0;
-    int k = 1;
+    // the first iteration: 1, or the one after the main solve's last
+    const int k0 = a.resume ? ld_relaxed_i32(&a.ctl->iterations) + 1 : 1;
+    int k = k0;
     int fb_local = 0;
     unsigned int my_faces = 0;
     __shared__ int s_ncand;
+    // max_iters bounds the iteration numbers, so it bounds the main and the
+    // resumed solve together
     for (; k <= a.max_iters; ++k) {
         const int cur = k % 3, nxt = (k + 1) % 3, nn = (k + 2) % 3;
         // one read of the list size per CTA (all warps reading the one word
@@ -258,17 +270,17 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
         int *nlist = a.lists + (int64_t)nxt * a.n_tot;
         // a front smaller than a third of the 8-lane groups: one warp per
         // vertex, so a vertex's faces take one round instead of three
-        if ((int64_t)n_cand * 3 <= ngroups) {
-            for (int64_t g = gwarp;; g += nwarps) {
+        if (n_cand <= ngroups / 3) {
+            for (int g = gwarp;; g += nwarps) {
                 const bool act = g < n_cand;
                 if (!__any_sync(0xffffffffu, act)) break;
-                fim_vertex<MODE, 32>(a, k, g, act, list, nlist, nxt, s_list, &s_n, fb_local, my_faces);
+                fim_vertex<MODE, DEFER, 32>(a, k, g, act, list, nlist, nxt, s_list, &s_n, fb_local, my_faces);
             }
         } else {
-            for (int64_t g = ggroup;; g += ngroups) {
+            for (int g = ggroup;; g += ngroups) {
                 const bool act = g < n_cand;
                 if (!__any_sync(0xffffffffu, act)) break;
-                fim_vertex<MODE, FIM_G>(a, k, g, act, list, nlist, nxt, s_list, &s_n, fb_local, my_faces);
+                fim_vertex<MODE, DEFER, FIM_G>(a, k, g, act, list, nlist, nxt, s_list, &s_n, fb_local, my_faces);
             }
         }
         // flush the CTA's appends with one global reservation
@@ -305,6 +317,89 @@ __global__ void __launch_bounds__(FIM_BLOCK, FIM_MINB) k_fim(FimArgs a)
             if (k > a.max_iters && !ld_relaxed_i32(&a.ctl->abort))
                 atomicCAS(&a.ctl->status, 0, (int)GBP_ERR_NOT_CONVERGED);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 repair of the faces the main solve deferred.  The main solve converged
+// to a fixed point U of the operator that takes the boundary minimum of
+// those faces (an upper bound of theirs), and each face's last evaluation
+// used the final values of its vertices, so the deferred faces that matter
+// are in the list.  Each is solved in full with U's values; a vertex whose
+// value drops takes it (smallest (value, code) per vertex), and the exact
+// iteration resumes from its neighbours: monotone iteration from an upper
+// bound ends at the same fixed point the exact solve would.
+// ---------------------------------------------------------------------------
+__global__ void k_repair_init(FimArgs a, unsigned long long *keys)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < min(ld_relaxed_i32(&a.ctl->n_defer), FIM_DEFER_CAP)) keys[a.defer[d].x] = ~0ull;
+}
+
+__global__ void k_repair(FimArgs a, unsigned long long *keys)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= min(ld_relaxed_i32(&a.ctl->n_defer), FIM_DEFER_CAP)) return;
+    const int2 de = a.defer[d];
+    const int gi = de.x, n_v = (int)a.n_v;
+    const int b = gi / n_v, boff = b * n_v, toff = b * (int)a.n_t;
+    const int4 fr = a.frec[de.y];
+    const float ph[3] = {__int_as_float(a.pc[boff + fr.x].x), __int_as_float(a.pc[boff + fr.y].x),
+                         __int_as_float(a.pc[boff + fr.z].x)};
+    const int j = fr.w >> 2;
+    const float2 vj = a.tv[toff + j];
+    const float4 fj = a.tf[j];
+    const float4 m = make_float4(fj.x, fj.y, fj.z, vj.x);
+    const float4 xi = a.xyz[gi - boff];
+    const float4 x0 = a.xyz[fr.x], x1 = a.xyz[fr.y], x2 = a.xyz[fr.z];
+    float3 p[3];
+    p[0] = xform(make_float3(x0.x - xi.x, x0.y - xi.y, x0.z - xi.z), m, vj.y);
+    p[1] = xform(make_float3(x1.x - xi.x, x1.y - xi.y, x1.z - xi.z), m, vj.y);
+    p[2] = xform(make_float3(x2.x - xi.x, x2.y - xi.y, x2.z - xi.z), m, vj.y);
+    int fb = 0;
+    const LocalRes res = local_exact(p, ph, &fb);
+    if (fb) atomicAdd(&a.ctl->fp64_fallbacks, (unsigned long long)fb);
+    if (res.v < __int_as_float(a.pc[gi].x))
+        atomicMin(&keys[gi], ((unsigned long long)float_key(res.v) << 32) | (unsigned int)fr.w);
+}
+
+__global__ void k_repair_apply(FimArgs a, unsigned long long *keys)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= min(ld_relaxed_i32(&a.ctl->n_defer), FIM_DEFER_CAP)) return;
+    const int gi = a.defer[d].x;
+    // one thread per vertex takes its key
+    const unsigned long long K = atomicExch(&keys[gi], ~0ull);
+    if (K == ~0ull) return;
+    const float v = key_float((unsigned int)(K >> 32));
+    const int code = (int)(K & 0xffffffffu);
+    const int k0 = ld_relaxed_i32(&a.ctl->iterations) + 1;
+    const int2 own = a.pc[gi];
+    const float phi_old = __int_as_float(own.x);
+    if (!(v < phi_old)) return;
+    const bool changed = (phi_old == GBP_INF) || (phi_old - v > a.eps);
+    a.pc[gi] = make_int2(__float_as_int(v), changed ? k0 - 1 : own.y);
+    a.rec[gi].x = code;
+    atomicAdd(&a.ctl->n_repaired, 1);
+    if (!changed) return;
+    const int n_v = (int)a.n_v, boff = (gi / n_v) * n_v, i = gi - boff;
+    int *list = a.lists + (int64_t)(k0 % 3) * a.n_tot;
+    for (int e = a.n2n_ptr[i]; e < a.n2n_ptr[i + 1]; ++e) {
+        const int mm = boff + a.n2n[e];
+        if (atomicMax(&a.stamp[mm], k0) < k0) list[atomicAdd(&a.ctl->count[k0 % 3], 1)] = mm;
+    }
+}
+
+// More deferred faces than the list holds (not seen on the test meshes): the
+// resumed exact iteration starts from every vertex, all faces masked in.
+__global__ void k_repair_all(FimArgs a)
+{
+    if (!ld_relaxed_i32(&a.ctl->defer_overflow)) return;
+    const int k0 = ld_relaxed_i32(&a.ctl->iterations) + 1;
+    int *list = a.lists + (int64_t)(k0 % 3) * a.n_tot;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < (int)a.n_tot; g += gridDim.x * blockDim.x) {
+        a.pc[g].y = k0 - 1;
+        if (atomicMax(&a.stamp[g], k0) < k0) list[atomicAdd(&a.ctl->count[k0 % 3], 1)] = g;
     }
 }
 
@@ -362,14 +457,39 @@ cudaError_t launch_fim(gbp_ctx *c, const gbp_solve_opts *o)
     a.max_iters = o->max_iters;
     a.n_f = o->n_f;
     a.trace = trace;
+    a.defer = c->defer;
+    a.resume = 0;
     err = cudaMemsetAsync(c->bar_grp, 0, sizeof(BarGroup) * GBP_BAR_GROUPS, c->stream);
     if (err) return err;
-    const void *fn = o->local_solver == GBP_LOCAL_FISTA ? (const void *)k_fim<GBP_LOCAL_FISTA>
-                                                        : (const void *)k_fim<GBP_LOCAL_EXACT>;
+    const bool exact = o->local_solver != GBP_LOCAL_FISTA;
+    const void *fn = exact ? (const void *)k_fim<GBP_LOCAL_EXACT, true> : (const void *)k_fim<GBP_LOCAL_FISTA, false>;
     int grid = fim_grid(c, fn);
     void *args[] = {&a};
     time_begin(c, 0);
     err = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(FIM_BLOCK), args, 0, c->stream);
+    if (!err && exact) {
+        // the deferred faces in FP64, then the exact iteration from what they
+        // lowered (an empty list ends it at once)
+        const unsigned bl = FIM_DEFER_CAP / 256;
+        k_repair_init<<<bl, 256, 0, c->stream>>>(a, c->keys);
+        k_repair<<<bl, 256, 0, c->stream>>>(a, c->keys);
+        k_repair_apply<<<bl, 256, 0, c->stream>>>(a, c->keys);
+        k_repair_all<<<c->num_sms, 256, 0, c->stream>>>(a);
+        c->launches += 4;
+        err = cudaGetLastError();
+        // the resumed kernel numbers its grid barriers from 1 again: zero the
+        // grid-level arrival count and the groups' words (the abort flag is
+        // kept, so a main solve that gave up ends the resumed one at once)
+        if (!err) err = cudaMemsetAsync(&c->ctl->barrier, 0, sizeof(unsigned int), c->stream);
+        if (!err) err = cudaMemsetAsync(c->bar_grp, 0, sizeof(BarGroup) * GBP_BAR_GROUPS, c->stream);
+        if (!err) {
+            a.resume = 1;
+            a.trace = nullptr;
+            const void *fr = (const void *)k_fim<GBP_LOCAL_EXACT, false>;
+            err = cudaLaunchCooperativeKernel(fr, dim3(fim_grid(c, fr)), dim3(FIM_BLOCK), args, 0, c->stream);
+            c->launches++;
+        }
+    }
     time_end(c, 0);
     c->launches++;
     if (err) return err;

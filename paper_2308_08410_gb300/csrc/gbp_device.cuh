@@ -47,7 +47,9 @@ struct Control {
     float adj_xmax[3];            // max |x| of the cycle iteration (rotating slots)
     double adj_lsum;              // sum |dL/dphi| (scale of the adjoint's fixed-point sums)
     unsigned long long adj_ts[3]; // global timer at adjoint start, end of dataflow, end
-    int pad[3];
+    int n_defer;                  // FIM faces deferred to the FP64 repair (entries written, may exceed the cap)
+    int defer_overflow;           // more deferred faces than the list holds: the repair re-solves everything
+    int n_repaired;               // vertices the repair lowered
     int param_status;             // latched by the metric precompute (kept across solves)
 };
 
@@ -165,12 +167,16 @@ __device__ __forceinline__ double eval_candidate64(const float3 p[3], const floa
 
 // Interior stationary point of the face (all three values finite), FP64.
 // Same algebra as the FP32 branch below; used when the FP32 discriminant
-// or the face is too close to degenerate.  Scalar arguments keep the caller's
-// operands in registers.
-static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0z, float p1x, float p1y, float p1z,
-                                                  float p2x, float p2y, float p2z, float ph0, float ph1, float ph2,
-                                                  float *b0o, float *b1o)
+// or the face is too close to degenerate.  Scalar arguments and a by-value
+// result keep the caller's operands in registers; returns (beta0, beta1), or
+// (-1, -1) when the point is not inside.  Inlined: an out-of-line call in the
+// FIM's face loop made the register allocator spill the loop's state on every
+// face; the FIM defers these solves to after its face loop instead
+// (local_exact with DEFER64).
+static __device__ __forceinline__ float2 interior_fp64(float p0x, float p0y, float p0z, float p1x, float p1y, float p1z,
+                                                    float p2x, float p2y, float p2z, float ph0, float ph1, float ph2)
 {
+    const float2 none = make_float2(-1.f, -1.f);
     double d1x = (double)p0x - p2x, d1y = (double)p0y - p2y, d1z = (double)p0z - p2z;
     double d2x = (double)p1x - p2x, d2y = (double)p1y - p2y, d2z = (double)p1z - p2z;
     double Q00 = d1x * d1x + d1y * d1y + d1z * d1z;
@@ -178,22 +184,20 @@ static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0
     double Q11 = d2x * d2x + d2y * d2y + d2z * d2z;
     double nx = d1y * d2z - d1z * d2y, ny = d1z * d2x - d1x * d2z, nz = d1x * d2y - d1y * d2x;
     double det = nx * nx + ny * ny + nz * nz;
-    if (!(det > 0.0)) return false;
+    if (!(det > 0.0)) return none;
     double q0 = d1x * p2x + d1y * p2y + d1z * p2z;
     double q1 = d2x * p2x + d2y * p2y + d2z * p2z;
     double D0 = (double)ph0 - ph2, D1 = (double)ph1 - ph2;
     double k = (Q11 * D0 * D0 - 2.0 * Q01 * D0 * D1 + Q00 * D1 * D1) / det;
     double tp = nx * p2x + ny * p2y + nz * p2z;
     double S = tp * tp / det;
-    if (!(k < 1.0) || !(S > 0.0)) return false;
+    if (!(k < 1.0) || !(S > 0.0)) return none;
     double h = sqrt(S / (1.0 - k));
     double y0 = h * D0 + q0, y1 = h * D1 + q1;
     double b0 = -(Q11 * y0 - Q01 * y1) / det;
     double b1 = -(-Q01 * y0 + Q00 * y1) / det;
-    if (!(b0 > 0.0 && b1 > 0.0 && b0 + b1 < 1.0)) return false;
-    *b0o = (float)b0;
-    *b1o = (float)b1;
-    return true;
+    if (!(b0 > 0.0 && b1 > 0.0 && b0 + b1 < 1.0)) return none;
+    return make_float2((float)b0, (float)b1);
 }
 
 // The interior step is redone in FP64 when 1 - Delta^T Q^-1 Delta falls below
@@ -223,8 +227,13 @@ static __device__ __noinline__ bool interior_fp64(float p0x, float p0y, float p0
 // alpha differ in value by less than FP32 resolves (a fraction of an ulp),
 // while FP64 separates them; a plain FP32 comparison returns the same value
 // but the other candidate's alpha.
-template <bool ALPHA = false>
-__device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float ph[3], int *fb)
+//
+// DEFER64 (the FIM's face loop): a face whose interior step needs FP64 is not
+// solved in FP64 here; *need64 is set and the boundary minimum (an upper
+// bound of the face's value) is returned, and the caller solves the face
+// again in full where fewer registers are live.
+template <bool ALPHA = false, bool DEFER64 = false>
+__device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float ph[3], int *fb, bool *need64 = nullptr)
 {
     LocalRes r;
     r.v = GBP_INF;
@@ -257,10 +266,15 @@ __device__ __forceinline__ LocalRes local_exact(const float3 p[3], const float p
         if ((k < 1.f && !outside) || degenerate) {
             float b0, b1;
             bool found = false;
-            if (degenerate || near_singular) {
+            if ((degenerate || near_singular) && DEFER64) {
+                *need64 = true;
+            } else if (degenerate || near_singular) {
                 ++*fb;
-                found = interior_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y, p[2].z, ph[0],
-                                      ph[1], ph[2], &b0, &b1);
+                const float2 bb = interior_fp64(p[0].x, p[0].y, p[0].z, p[1].x, p[1].y, p[1].z, p[2].x, p[2].y,
+                                                p[2].z, ph[0], ph[1], ph[2]);
+                b0 = bb.x;
+                b1 = bb.y;
+                found = b0 > 0.f;
             } else {
                 float h = lsqrt(S * __fdividef(1.f, 1.f - k));
                 float y0 = fmaf(h, D0, q0), y1 = fmaf(h, D1, q1);

@@ -67,6 +67,7 @@ struct gbp_ctx {
     gbp::Control *h_ctl = nullptr;  // pinned
     int last_mode = 0, last_nf = 0;
     int64_t param_gen = 0, solve_gen = -1;
+    int2 *defer = nullptr;  // FIM faces deferred to the FP64 repair: (vertex entry, face record index)
     int rec_nb = 0;  // problems held in the solution (phi, parent record) of the last solve (0: none)
     // adjoint state
     float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;
@@ -107,6 +108,8 @@ struct gbp_ctx {
 };
 
 namespace gbp {
+// capacity of the FIM's list of faces deferred to the FP64 repair
+constexpr int FIM_DEFER_CAP = 1 << 16;
 // launch helpers implemented in the .cu files (all stream-ordered)
 cudaError_t launch_precompute(gbp_ctx *c);
 cudaError_t launch_lipschitz(gbp_ctx *c);

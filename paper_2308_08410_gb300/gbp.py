@@ -43,7 +43,7 @@ class SolveStats(C.Structure):
                 ("fp64_fallbacks", C.c_int64), ("unreached", C.c_int64), ("adj_levels", C.c_int64),
                 ("adj_cycle_nodes", C.c_int64), ("adj_cycle_iters", C.c_int64),
                 ("status", C.c_int32), ("reserved", C.c_int32), ("adj_dataflow_ms", C.c_double),
-                ("adj_cycle_ms", C.c_double)]
+                ("adj_cycle_ms", C.c_double), ("fim_deferred", C.c_int64), ("fim_repaired", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}

@@ -129,7 +129,9 @@ class InverseProblem:
         self.x.copy_(torch.einsum("kq,kqr->kr", b, V))
 
     def run_adam(self, iters=500, lr=1e-2, log_every=0, callback=None, lr_sites=None):
-        """Adam at lr; onset times and positions at lr_sites when given."""
+        """Adam at lr; onset times and positions at lr_sites when given.  A
+        callback(iteration, loss) that returns True ends the run after that
+        iteration."""
         if lr_sites is None:
             opt = torch.optim.Adam(self.params(), lr=lr)
         else:
@@ -146,8 +148,10 @@ class InverseProblem:
             self.project_positions()
             if log_every and (it % log_every == 0 or it == iters - 1):
                 hist.append((it, float(loss.item()), time.perf_counter() - t_start))
-            if callback is not None:
-                callback(it, loss)
+            if callback is not None and callback(it, loss):
+                if log_every and hist and hist[-1][0] != it:
+                    hist.append((it, float(loss.item()), time.perf_counter() - t_start))
+                break
         torch.cuda.synchronize()
         return hist, time.perf_counter() - t_start
 

@@ -147,6 +147,23 @@ def kuhn_cube(n: int, side: float = 10.0) -> Mesh:
     return Mesh(xyz.astype(np.float32), tets)
 
 
+def kuhn_slab(n: int, layers: int, hz: float, side: float = 10.0) -> Mesh:
+    """The bottom `layers` vertex layers of the n^3 Kuhn cube on [0, side]^3,
+    with the layer spacing squashed to hz (mm): a slab of sliver tets whose
+    vertices lie close to the planes of their opposite faces."""
+    m = kuhn_cube(n, side)
+    xyz = m.xyz.astype(np.float64)
+    h = side / (n - 1)
+    keep_v = xyz[:, 2] <= (layers - 1) * h + 1e-9
+    keep_t = keep_v[m.tets].all(axis=1)
+    idx = -np.ones(len(xyz), np.int64)
+    idx[keep_v] = np.arange(int(keep_v.sum()))
+    tets = idx[m.tets[keep_t]].astype(np.int32)
+    xyz = xyz[keep_v]
+    xyz[:, 2] *= hz / h
+    return Mesh(xyz.astype(np.float32), tets)
+
+
 def voxel_kuhn(mask: np.ndarray, h: float, origin) -> Mesh:
     """Kuhn-split every voxel cell with mask[i,j,k] True (cell spans
     origin + h*[i,i+1] x ...).  Unused grid nodes are dropped."""

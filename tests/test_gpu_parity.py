@@ -189,6 +189,26 @@ def test_eikonal_eps_and_unreached(ctx):
     assert np.all(par[a.n_v:] == gbp.UNREACHED)
 
 
+def test_eikonal_sliver_slab_fp64_repair(ctx):
+    """A slab of sliver tets (16 x 16 x 3 vertices, layers 0.005 mm apart
+    against 0.67 mm in the plane): many local problems have their interior
+    stationary point at 1 - k < 1e-3, the case the exact solver takes to FP64,
+    and some of those points are inside their face and are the vertex's
+    minimiser.  The FIM leaves these faces to its FP64 repair (an upper bound
+    meanwhile), which re-solves them and resumes the exact iteration from the
+    vertices it lowers: phi and parents must still equal the oracle's."""
+    mesh = S.kuhn_slab(16, 3, 0.005)
+    n_t = mesh.n_t
+    r = np.random.default_rng(1)
+    fib = np.tile(np.array([[0.8, 0.6, 0.0]], np.float32), (n_t, 1))
+    cf = (0.6 * (1 + 0.05 * r.standard_normal(n_t))).astype(np.float32)
+    ct = (0.3 * (1 + 0.05 * r.standard_normal(n_t))).astype(np.float32)
+    ons = S.Onsets(S.ONSET_NODAL, np.array([0, mesh.n_v // 2], np.int32), np.array([0.0, 3.0], np.float32))
+    p = S.Problem("slab", mesh, fib, cf, ct, ons, np.ones((1, mesh.n_v), np.float32), S.Template(T=8))
+    g, par, al, ref, st = check_eikonal(ctx, p)
+    assert st["fim_deferred"] > 0 and st["fim_repaired"] > 0, st
+
+
 @pytest.mark.parametrize("n_f", [32, 48])
 @pytest.mark.parametrize("jitter", [False, True])
 def test_eikonal_fista_mode(ctx, n_f, jitter):

@@ -56,6 +56,7 @@ int main(void)
     F(gbp_solve_stats, fp64_fallbacks); F(gbp_solve_stats, unreached); F(gbp_solve_stats, adj_levels);
     F(gbp_solve_stats, adj_cycle_nodes); F(gbp_solve_stats, adj_cycle_iters); F(gbp_solve_stats, status);
     F(gbp_solve_stats, reserved); F(gbp_solve_stats, adj_dataflow_ms); F(gbp_solve_stats, adj_cycle_ms);
+    F(gbp_solve_stats, fim_deferred); F(gbp_solve_stats, fim_repaired);
     F(gbp_template, K0); F(gbp_template, K1); F(gbp_template, tau); F(gbp_template, t0); F(gbp_template, dt);
     F(gbp_template, T);
     printf("const LOCAL_EXACT %d\nconst LOCAL_FISTA %d\n", GBP_LOCAL_EXACT, GBP_LOCAL_FISTA);
@@ -96,7 +97,7 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
             desc = getattr(structs[sname], field)
             assert (desc.offset, desc.size) == (int(vals[0]), int(vals[1])), line
         seen += 1
-    assert seen == 3 + 22 + 7
+    assert seen == 3 + 24 + 7
 
 
 def _c_kind(decl):
