@@ -331,9 +331,14 @@ __device__ __forceinline__ int ld_acquire_i32(const int *p)
     return v;
 }
 
+#ifndef GBP_ADJ_POST
+#define GBP_ADJ_POST 4  // vertices per thread and step of the gradient pass after the dataflow
+#endif
+constexpr int ADJ_POST = GBP_ADJ_POST;
 #ifndef GBP_ADJ_REFILL
 #define GBP_ADJ_REFILL 8  // idle lanes that make a warp take new items while others are busy
 #endif
+
 
 __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
 {
@@ -442,7 +447,10 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
                         const unsigned long long d = (unsigned long long)c - ADJ_ONE;
                         nw[q] = atomicAdd(&a.w[boff + r.f[q]], d) + d;
                     }
-                    local_terms(a, b, v - boff, r, m);
+                    // a 2-cycle member's mu is not its word's sum: its
+                    // gradient terms are added here; every other vertex's
+                    // after the dataflow (below)
+                    if (r.jt & ADJ_PAIR_FLAG) local_terms(a, b, v - boff, r, m);
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
                         if (r.f[q] < 0 || boff + r.f[q] == partner || adj_count(nw[q]) != 0u) continue;
@@ -542,6 +550,35 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     // ---- vertices blocked by cycles: fixed-point iteration ----
     // collect the unprocessed reached vertices R (closed under parents); the
     // barrier above ordered every write of the dataflow phase before this
+    // The gradient terms of the vertices the dataflow finished with a face
+    // parent (2-cycle members excepted), in vertex order: their mu is the
+    // complete sum in their word.  Scattered through the dataflow, these float
+    // atomics into the per-tet gradients (arrays larger than L2 at 16
+    // problems) slowed its chains by ~30 %.  ADJ_POST vertices per thread
+    // and step, every load issued before the atomics, so that the loads
+    // overlap.
+    for (int64_t base = 0; base < n_tot; base += ADJ_POST * nth) {
+        ARec r[ADJ_POST];
+        unsigned long long wv[ADJ_POST];
+        bool ok[ADJ_POST];
+#pragma unroll
+        for (int u = 0; u < ADJ_POST; ++u) {
+            const int64_t i = base + u * nth + tid;
+            ok[u] = i < n_tot && is_done(a.done, i);
+            if (ok[u]) {
+                r[u] = load_arec(a.arec, i);
+                wv[u] = __ldcg(&a.w[i]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < ADJ_POST; ++u) {
+            const int64_t i = base + u * nth + tid;
+            if (ok[u] && r[u].jt >= 0 && !(r[u].jt & ADJ_PAIR_FLAG)) {
+                const int b = (int)(i / n_v);
+                local_terms(a, b, i - (int64_t)b * n_v, r[u], (float)((double)adj_sum(wv[u]) * iscale));
+            }
+        }
+    }
     int *R = a.lists + 3 * n_tot;
     for (int64_t base = 0; base < n_tot; base += nth) {
         const int64_t i = base + tid;
