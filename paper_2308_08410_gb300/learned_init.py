@@ -686,6 +686,43 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
                 reached=int(sum(bool(np.isfinite(r["learned_time"])) for r in rows)))
 
 
+# The network's GEMM shapes at the training minibatch of 256 (M, N, K): the
+# first convolution (256 x 150 output positions, 64 channels, 12 leads x 5
+# taps padded to 64), a later convolution (64 channels x 5 taps), the hidden
+# layer; and one large square product that shows the kernel itself.
+GEMM_SHAPES = ((38400, 64, 64), (19200, 64, 320), (256, 256, 1216), (8192, 8192, 4096))
+
+
+def gemm_rates(ctx: gbp.Context, shapes=GEMM_SHAPES, reps: int = 20) -> list:
+    """Achieved TFLOP/s of the tcgen05 BF16 GEMM (gbp_nn_gemm_bf16) per shape:
+    CUDA events on the context stream around `reps` calls after 3 warm-up
+    calls; 2 M N K flops per call."""
+    lib, dev, st = ctx.lib, ctx.torch_device, ctx.stream
+    out = []
+    for M, N, K in shapes:
+        Kp = _r64(K)
+        g = torch.Generator(device=dev).manual_seed(0)
+        A = torch.randn(M, Kp, device=dev, generator=g).to(torch.bfloat16)
+        Bm = torch.randn(N, Kp, device=dev, generator=g).to(torch.bfloat16)
+        Cm = torch.empty(M, N, device=dev, dtype=torch.float32)
+
+        def call():
+            gbp._check(lib.gbp_nn_gemm_bf16(ctx.h, M, N, Kp, _p(A), Kp, _p(Bm), Kp, _p(Cm), N, 1.0, 0.0),
+                       "gbp_nn_gemm_bf16")
+        for _ in range(3):
+            call()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(st)
+        for _ in range(reps):
+            call()
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"M": M, "N": N, "K": K, "us": ms * 1e3, "tflops": 2.0 * M * N * Kp / (ms * 1e-3) / 1e12})
+    return out
+
+
 def summary(res) -> dict:
     """One JSON record of the experiment: time to the plain FP32 arm's best
     misfit for learned init + BF16 ECG (misses count as never), the misfits
@@ -724,7 +761,21 @@ if __name__ == "__main__":
     ap.add_argument("--no-relocate", action="store_true", help="keep every onset inside its initial tet")
     ap.add_argument("--json", action="store_true",
                     help="print one JSON summary line (cases reached, median seconds, misfits at arrival)")
+    ap.add_argument("--gemm", action="store_true",
+                    help="only time the BF16 GEMM at the network's shapes and one large square shape (JSON)")
     a = ap.parse_args()
+    if a.gemm:
+        import os
+        peak = None
+        mp = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "MEASURED_PEAKS.json")
+        if os.path.exists(mp):
+            with open(mp) as f:
+                peak = json.load(f).get("bf16_tflops")
+        rows = gemm_rates(gbp.Context(0))
+        for r in rows:
+            r["frac_of_measured_bf16"] = r["tflops"] / peak if peak else None
+        print(json.dumps({"kernel": "k_gemm_tn", "peak_bf16_tflops_measured": peak, "shapes": rows}))
+        raise SystemExit(0)
     res = run_experiment(a.train, a.test, a.epochs, a.eval, a.iters, relocate=not a.no_relocate,
                          log=(lambda *_: None) if a.json else print)
     s = json.dumps(summary(res) if a.json else res)
