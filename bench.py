@@ -23,6 +23,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -420,14 +421,19 @@ KERNEL_SOURCES = {
 TRAFFIC_FILES = {"k_fim": "fim_traffic_c3_batch{batch}.txt", "k_adjoint": "adjoint_traffic_c3_batch{batch}.txt"}
 
 
+_COMMENT = re.compile(r'("(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\')|//[^\n]*|/\*.*?\*/', re.S)
+
+
 def kernel_hash(kernel: str = "k_fim") -> str:
-    """Hash of a kernel's sources: a stored ncu traffic figure applies only
-    while it matches."""
+    """Hash of a kernel's sources with their comments taken out (string
+    literals, such as inline PTX, kept) and runs of white space made one
+    space: a stored ncu traffic figure applies only while it matches."""
     import hashlib
     h = hashlib.sha1()
     for f in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), encoding="utf-8") as fh:
+            code = _COMMENT.sub(lambda m: m.group(1) or "", fh.read())
+        h.update(" ".join(code.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -39,10 +39,12 @@
 //
 // Memory: a hop reads the vertex's 32-byte record written by the parent pass
 // (parent vertices, alpha, the tet and its two velocity coefficients: one
-// sector) and does its atomics: the pushes into the parents' words, which
-// also hold lambda in the same fixed point (so the vertex that completes a
-// parent reads its whole mu from the atomic's return value), and the two
-// gradient additions.  Processed vertices are marked in a bitmap.
+// sector) and does its pushes into the parents' words, which also hold lambda
+// in the same fixed point (so the vertex that completes a parent reads its
+// whole mu from the atomic's return value).  Processed vertices are marked in
+// a bitmap.  The gradient additions of the vertices with a face parent follow
+// the dataflow in one pass in vertex order (their mu is then the sum in their
+// word); only 2-cycle members and onset-parented vertices add theirs inline.
 #include "gbp_internal.cuh"
 
 namespace gbp {
