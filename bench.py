@@ -424,16 +424,20 @@ TRAFFIC_FILES = {"k_fim": "fim_traffic_c3_batch{batch}.txt", "k_adjoint": "adjoi
 _COMMENT = re.compile(r'("(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\')|//[^\n]*|/\*.*?\*/', re.S)
 
 
+def normalize_source(text: str) -> str:
+    """C/C++/CUDA source with its comments taken out (string literals, such as
+    inline PTX, kept) and every run of white space made one space."""
+    return " ".join(_COMMENT.sub(lambda m: m.group(1) or "", text).split())
+
+
 def kernel_hash(kernel: str = "k_fim") -> str:
-    """Hash of a kernel's sources with their comments taken out (string
-    literals, such as inline PTX, kept) and runs of white space made one
-    space: a stored ncu traffic figure applies only while it matches."""
+    """Hash of a kernel's normalised sources (normalize_source): a stored ncu
+    traffic figure applies only while it matches."""
     import hashlib
     h = hashlib.sha1()
     for f in KERNEL_SOURCES[kernel]:
         with open(os.path.join(ROOT, "paper_2308_08410_gb300", "csrc", f), encoding="utf-8") as fh:
-            code = _COMMENT.sub(lambda m: m.group(1) or "", fh.read())
-        h.update(" ".join(code.split()).encode())
+            h.update(normalize_source(fh.read()).encode())
     return h.hexdigest()[:12]
 
 
