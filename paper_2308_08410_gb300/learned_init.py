@@ -689,8 +689,9 @@ def run_experiment(n_train=20000, n_test=2000, epochs=60, n_eval=20, iters=300, 
 # The network's GEMM shapes at the training minibatch of 256 (M, N, K): the
 # first convolution (256 x 150 output positions, 64 channels, 12 leads x 5
 # taps padded to 64), a later convolution (64 channels x 5 taps), the hidden
-# layer; and one large square product that shows the kernel itself.
-GEMM_SHAPES = ((38400, 64, 64), (19200, 64, 320), (256, 256, 1216), (8192, 8192, 4096))
+# layer; and two larger products (the TMA-fed kernel) that show the kernels
+# themselves.
+GEMM_SHAPES = ((38400, 64, 64), (19200, 64, 320), (256, 256, 1216), (2048, 2048, 2048), (8192, 8192, 4096))
 
 
 def gemm_rates(ctx: gbp.Context, shapes=GEMM_SHAPES, reps: int = 20) -> list:

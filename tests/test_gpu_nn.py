@@ -1,8 +1,9 @@
 """The learned initialiser's kernels (gbp_nn_*, tcgen05 BF16 GEMM + elementwise
 kernels) against the FP64 reference network (oracle/nn_oracle.py).
 
-Tolerances: the GEMM against an FP64 product of the same BF16-rounded
-operands (FP32 accumulation: 1e-5 relative); the whole network (every GEMM
+Tolerances: the GEMM (both kernels: the 128 x 64 tile kernel and, for
+shapes of at least 64 whole 128 x 256 tiles, the TMA-fed one) against an FP64 product of
+the same BF16-rounded operands (FP32 accumulation: 1e-5 relative); the whole network (every GEMM
 operand rounded to BF16, 2^-9 relative each, through six layers) against the
 FP64 reference with FP32 weights: 3e-2 relative L2 for outputs and
 gradients."""
@@ -38,7 +39,9 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32)
 
 
-@pytest.mark.parametrize("M,N,K", [(300, 100, 130), (128, 64, 64), (1, 43, 256), (1000, 320, 1216)])
+# the last two are 64 and 72 whole 128 x 256 tiles: the TMA-fed kernel
+@pytest.mark.parametrize("M,N,K", [(300, 100, 130), (128, 64, 64), (1, 43, 256), (1000, 320, 1216),
+                                   (1024, 2048, 320), (1152, 2048, 1216)])
 def test_gemm_bf16(ctx, M, N, K):
     rng = np.random.default_rng(M + N + K)
     Kp = ((K + 63) // 64) * 64
