@@ -203,3 +203,83 @@ def test_batch_host_entry_point(ctx):
         for k in ("loss", "d_cf", "d_ct", "d_t", "d_x"):
             assert h[k].shape == d[k].shape, k
             assert rel_l2(h[k], d[k]) < 1e-5, (pinned, k)
+
+
+@pytest.mark.parametrize("n_f", [32, 64])
+def test_batch_fista_mode(ctx, n_f):
+    """Algorithm 1 as the local solver inside a batched call.  Each problem's
+    phi against the oracle's FISTA-mode eikonal at the same n_f in Algorithm
+    2's own (Jacobi) order, at the single-problem test's 5e-6 (a fixed-n_f
+    Algorithm 1 is not monotone, so its fixed point depends on the order),
+    and its loss against the oracle's misfit of that solution (1e-4).
+
+    Gradients: the GPU's parent of a vertex is the face whose solve produced
+    its value; the oracle's is the face with the smallest value at the final
+    values.  For the exact solver these coincide (monotone iteration, fixed
+    point); a fixed-n_f Algorithm 1 is not monotone, so the value set by one
+    face can stay below every face's value at the end and the two can name
+    different faces (a few vertices per problem at n_f = 32, none seen at
+    64).  Per tet, d_cf and d_ct are held to 1e-3 |r| + 1e-6 max |r| on every
+    tet no such vertex touches (the tie rule of the exact-solver tests); the
+    whole vectors, and d_t, to 1e-3 where no parent differs, d_t to 1e-2
+    where one does."""
+    B = 3
+    p, cf, ct, t, tg = batch_problem(10, B, seed=21, kind="nodal")
+    gbp.setup_problem(ctx, p)
+    opts = gbp.make_opts(local_solver=gbp.LOCAL_FISTA, n_f=n_f)
+    out = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(t), opts=opts)
+    assert ctx.stats()["status"] == 0
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    for b in range(B):
+        ons = S.Onsets(p.onsets.kind, p.onsets.idx, t[b], p.onsets.bary)
+        ek = O.eikonal(p.mesh, p.fib, cf[b], ct[b], ons, mode=O.FISTA, n_f=n_f, order=O.ORDER_JACOBI)
+        phi, par, _ = (x.cpu().numpy() for x in ctx.solution(b))
+        rel = np.abs(phi - ek["phi"]) / np.maximum(1, ek["phi"])
+        assert rel.max() < 5e-6, (b, rel.max())
+        V = O.ecg(p.L, ek["phi"], p.tmpl)
+        loss, lam = O.loss_grad_phi(p.L, ek["phi"], p.tmpl, V, tg[b])
+        ref = dict(ek)
+        ref.update(O.adjoint(p.mesh, p.fib, cf[b], ct[b], ons, ek["parent"], ek["alpha"], lam))
+        assert abs(g["loss"][b] - loss) / loss < 1e-4, (b, g["loss"][b], loss)
+        PH.check_tet_gradients({"d_cf": g["d_cf"][b], "d_ct": g["d_ct"][b]}, ref, par, p.mesh, ons)
+        if np.any(par != ek["parent"]):
+            assert rel_l2(g["d_t"][b], ref["d_t"]) < 1e-2
+        else:
+            for k in ("d_cf", "d_ct", "d_t"):
+                assert rel_l2(g[k][b], ref[k]) < 1e-3, (b, k, rel_l2(g[k][b], ref[k]))
+
+
+def test_batch_bf16_ecg(ctx):
+    """The batched call with the BF16 tensor-core ECG (problem by problem)
+    and the FP32 misfit and adjoint.  The eikonal is the FP32 call's, bit for
+    bit (the precision only changes the ECG forward); each problem's ECG is
+    the single-problem BF16 forward of its phi and stays within the BF16
+    error budget of the FP64 ECG (5e-2 relative L2, as for the single-problem
+    BF16 test); its loss and gradients are the oracle's misfit and adjoint
+    evaluated on that BF16 ECG (1e-4 and 1e-3, 1e-2 where a tie sent the GPU
+    to another face): the misfit of a BF16 ECG, not the FP32 one, is what the
+    call differentiates."""
+    B = 3
+    p, cf, ct, t, tg = batch_problem(12, B, seed=5)
+    gbp.setup_problem(ctx, p)
+    o32 = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(t))
+    phi32 = [ctx.solution(b)[0].cpu().numpy() for b in range(B)]
+    o16 = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(t), precision=gbp.PREC_BF16)
+    assert ctx.stats()["status"] == 0
+    g = {k: v.cpu().numpy() for k, v in o16.items()}
+    sols = [[x.cpu().numpy() for x in ctx.solution(b)] for b in range(B)]
+    for b in range(B):
+        phi, par, _ = sols[b]
+        np.testing.assert_array_equal(phi, phi32[b])
+        V1 = ctx.ecg_forward(dev(phi), p.tmpl, precision=gbp.PREC_BF16).cpu().numpy()
+        assert rel_l2(g["ecg"][b], V1) < 1e-6, rel_l2(g["ecg"][b], V1)
+        ons = S.Onsets(p.onsets.kind, p.onsets.idx, t[b], p.onsets.bary)
+        ek = O.eikonal(p.mesh, p.fib, cf[b], ct[b], ons)
+        assert rel_l2(g["ecg"][b], O.ecg(p.L, ek["phi"], p.tmpl)) < 5e-2
+        loss, lam = O.loss_grad_phi(p.L, ek["phi"], p.tmpl, g["ecg"][b].astype(np.float64), tg[b])
+        ref = O.adjoint(p.mesh, p.fib, cf[b], ct[b], ons, ek["parent"], ek["alpha"], lam)
+        assert abs(g["loss"][b] - loss) / loss < 1e-4, (b, g["loss"][b], loss)
+        tol = 1e-2 if np.any(par != ek["parent"]) else 1e-3
+        for k in ("d_cf", "d_ct", "d_t", "d_x"):
+            assert rel_l2(g[k][b], ref[k]) < tol, (b, k, rel_l2(g[k][b], ref[k]))
+    assert np.isfinite(o32["loss"].cpu().numpy()).all()
