@@ -114,3 +114,44 @@ def test_single_evaluation_at_the_benchmarked_point(workload):
         PH.check_tet_gradients(g, ref, par, p.mesh, ons)
     finally:
         ctx.close()
+
+
+def test_biv_batch_at_the_benchmarked_point():
+    """The biventricular shell of `bench.py --workload biv` (h = 1 mm: 95,199
+    vertices, 472,692 tets, 5 element onsets, 12 leads, T = 300) with the 16
+    starts that benchmark times (synth.c2_starts: a tissue velocity scale
+    exp(N(0, 0.1)) per start, 5 % per-tet log-velocity noise, onset times
+    +U(-2, 2) ms) through gbp_forward_backward_batch; three problems of the
+    batch against the oracle element by element, with the tolerances of the
+    cube test above (d_cf and d_ct as whole vectors at 1e-3 where no parent
+    differs from the oracle's)."""
+    p = S.make_c2(h=1.0, seed=0)
+    assert (p.mesh.n_v, p.mesh.n_t, p.onsets.K, p.L.shape[0], p.tmpl.T) == (95199, 472692, 5, 12, 300)
+    ek = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
+    target = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 4242).astype(np.float32)
+    cf, ct, t = S.c2_starts(p, B)
+    ctx = gbp.Context(0)
+    try:
+        gbp.setup_problem(ctx, p)
+        tg = np.repeat(target[None], B, axis=0)
+        out = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(t))
+        st = ctx.stats()
+        assert st["status"] == 0 and st["unreached"] == 0, st
+        g = {k: v.cpu().numpy() for k, v in out.items()}
+        for b in COMPARED:
+            ons = S.Onsets(p.onsets.kind, p.onsets.idx, t[b], p.onsets.bary)
+            ref = O.forward_backward(p.mesh, p.fib, cf[b], ct[b], ons, p.L, p.tmpl, target)
+            phi, par, al = (x.cpu().numpy() for x in ctx.solution(b))
+            PH.check_phi(phi, ref)
+            PH.check_parents(par, ref, min_unambiguous=0.95)
+            PH.check_alpha(al, par, p.mesh, p.fib, cf[b], ct[b], ref)
+            assert abs(g["loss"][b] - ref["loss"]) / ref["loss"] < 1e-4, (b, g["loss"][b], ref["loss"])
+            assert rel_l2(g["ecg"][b], ref["V"]) < 1e-3, b
+            for k in ("d_t", "d_x"):
+                assert rel_l2(g[k][b], ref[k]) < 1e-3, (b, k, rel_l2(g[k][b], ref[k]))
+            tol = 1e-2 if PH.parents_differ(par, ref) else 1e-3
+            for k in ("d_cf", "d_ct"):
+                assert rel_l2(g[k][b], ref[k]) < tol, (b, k, rel_l2(g[k][b], ref[k]))
+            PH.check_tet_gradients({"d_cf": g["d_cf"][b], "d_ct": g["d_ct"][b]}, ref, par, p.mesh, ons)
+    finally:
+        ctx.close()
