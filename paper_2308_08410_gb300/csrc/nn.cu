@@ -180,23 +180,18 @@ __global__ void __launch_bounds__(128) k_gemm_tn(int M, int N, int Kp, const __n
 }
 
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
 // The same product for shapes that fill 128 x 256 tiles exactly (M % 128 ==
 // 0, N % 256 == 0), fed by the tensor memory accelerator: A and B tiles of 64
 // K-columns land in shared memory by cp.async.bulk.tensor in the 128-byte
-// swizzled K-major layout (8-row atoms of 1024 bytes), four stages deep.  One
-// thread issues the copies (each stage's mbarrier counts their bytes), one
-// thread issues tcgen05.mma (M = 128, N = 256, K = 16 each, FP32 accumulator
-// in 256 TMEM columns) and frees each stage by committing to its "empty"
-// mbarrier; the last commit releases the epilogue, where the four warps read
-// their 32 TMEM lanes (rows) and write C.  Every wait is bounded: a wait that
-// runs out latches GBP_ERR_TIMEOUT, the copies in flight are waited for and
-// TMEM is freed before the CTA leaves.
+// swizzled K-major layout (8-row atoms of 1024 bytes), four stages deep, each
+// stage's mbarrier counting the copies' bytes; tcgen05.mma with M = 128,
+// N = 256, K = 16 per instruction and an FP32 accumulator in TMEM.
 constexpr int TM = 128, TN = 256, TK = 64, TS = 4;
 constexpr int TA_BYTES = TM * TK * 2;  // 16 KB
 constexpr int TB_BYTES = TN * TK * 2;  // 32 KB
 constexpr int T_STAGE = TA_BYTES + TB_BYTES;
 constexpr int T_SMEM = TS * T_STAGE + 1024;  // + slack to align the tiles to 1024 bytes
-constexpr uint32_t T_TMEM_COLS = 256;
 constexpr uint32_t T_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                              ((uint32_t)(TM >> 4) << 24);
 
@@ -222,29 +217,47 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map
         : "memory");
 }
 
-__global__ void __launch_bounds__(128) k_gemm_tma(int Kp, const __grid_constant__ CUtensorMap tA,
-                                                  const __grid_constant__ CUtensorMap tB, float *__restrict__ C,
-                                                  int ldc, float alpha, float beta, Control *ctl)
+// One CTA per SM walks the tiles (t = blockIdx.x, + gridDim.x, ...;
+// consecutive tiles share their B tile) with two 256-column accumulators in
+// TMEM, so that a tile's epilogue overlaps the next tile's MMAs and the
+// set-up is paid once per CTA.  Warp 0 (one lane) streams the copies through
+// the four stages across tile boundaries, warp 1 (one lane) issues the MMAs
+// into accumulator i & 1 and commits it to "acc full", warps 2-5 (TMEM lane
+// quadrants 2, 3, 0, 1) read it, write C and release it on "acc empty"; the
+// other lanes of warps 0 and 1 wait at __syncwarp (lanes of one warp that
+// poll an mbarrier hold the warp in each try_wait window: with them polling,
+// a first version ran at a quarter of this speed).  Every wait is bounded: a
+// wait that runs out latches GBP_ERR_TIMEOUT, the copies in flight and the
+// MMAs issued are waited for and TMEM is freed before the CTA leaves.
+constexpr uint32_t TP_TMEM_COLS = 512;
+
+__global__ void __launch_bounds__(192, 1) k_gemm_tma(int M, int N, int Kp, const __grid_constant__ CUtensorMap tA,
+                                                   const __grid_constant__ CUtensorMap tB, float *__restrict__ C,
+                                                   int ldc, float alpha, float beta, Control *ctl)
 {
     extern __shared__ __align__(1024) uint8_t t_smem[];
-    __shared__ __align__(8) uint64_t full[TS], empty[TS], done;
+    __shared__ __align__(8) uint64_t full[TS], empty[TS], accf[2], acce[2], done;
     __shared__ uint32_t s_tmem;
     __shared__ int s_fail;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tiles_m = M / TM, ntiles = tiles_m * (N / TN);
     const int steps = Kp / TK;
     const uint32_t base = (smem_u32(t_smem) + 1023u) & ~1023u;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                     "r"(T_TMEM_COLS)
+                     "r"(TP_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < TS; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+        for (int st = 0; st < TS; ++st) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[st])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[st])) : "memory");
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accf[b])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&acce[b])) : "memory");
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -253,111 +266,140 @@ __global__ void __launch_bounds__(128) k_gemm_tma(int Kp, const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = s_tmem;
-    // Warp 0's lane 0 issues the copies and warp 1's lane 0 the MMAs; their
-    // other lanes wait at __syncwarp meanwhile.  (Lanes of the same warp
-    // polling an mbarrier instead hold the warp in each try_wait window and
-    // starved the two issuing lanes: 1.8 us per K-step.)
-    int issued = 0;  // producer: stages issued
+    int issued = 0;  // producer: stages issued (over all tiles)
     if (warp == 0) {
-      if (tid == 0) {
-        for (int it = 0; it < steps; ++it) {
-            const int s = it % TS;
-            if (it >= TS && !g_mbar_wait(smem_u32(&empty[s]), (uint32_t)(((it / TS) & 1) ^ 1))) {
-                s_fail = 1;
-                break;
+        if (lane == 0) {
+            int g = 0;
+            bool bad = false;
+            for (int t = blockIdx.x; t < ntiles && !bad; t += gridDim.x) {
+                const int m0 = (t % tiles_m) * TM, n0 = (t / tiles_m) * TN;
+                for (int it = 0; it < steps; ++it, ++g) {
+                    const int st = g % TS;
+                    if (g >= TS && !g_mbar_wait(smem_u32(&empty[st]), (uint32_t)(((g / TS) & 1) ^ 1))) {
+                        bad = true;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full[st]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(T_STAGE)
+                                 : "memory");
+                    const uint32_t sa = base + (uint32_t)(st * T_STAGE);
+                    tma_load_2d(sa, &tA, it * TK, m0, fb);
+                    tma_load_2d(sa + TA_BYTES, &tB, it * TK, n0, fb);
+                    issued = g + 1;
+                }
             }
-            const uint32_t fb = smem_u32(&full[s]);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(T_STAGE) : "memory");
-            const uint32_t sa = base + (uint32_t)(s * T_STAGE);
-            tma_load_2d(sa, &tA, it * TK, m0, fb);
-            tma_load_2d(sa + TA_BYTES, &tB, it * TK, n0, fb);
-            issued = it + 1;
+            if (bad) s_fail = 1;
         }
-      }
-      __syncwarp();
+        __syncwarp();
     } else if (warp == 1) {
-      if (tid == 32) {
-        int it = 0;
-        for (; it < steps; ++it) {
-            const int s = it % TS;
-            if (!g_mbar_wait(smem_u32(&full[s]), (uint32_t)((it / TS) & 1))) {
-                s_fail = 1;
+        if (lane == 0) {
+            int g = 0, i = 0;
+            bool bad = false;
+            for (int t = blockIdx.x; t < ntiles && !bad; t += gridDim.x, ++i) {
+                const int buf = i & 1;
+                if (i >= 2 && !g_mbar_wait(smem_u32(&acce[buf]), (uint32_t)(((i >> 1) - 1) & 1))) {
+                    bad = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t acc = tmem + (uint32_t)(buf * 256);
+                for (int it = 0; it < steps; ++it, ++g) {
+                    const int st = g % TS;
+                    if (!g_mbar_wait(smem_u32(&full[st]), (uint32_t)((g / TS) & 1))) {
+                        bad = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = base + (uint32_t)(st * T_STAGE);
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; ++kk) {
+                        const uint64_t ad = sw128_desc(sa + 32u * kk);
+                        const uint64_t bd = sw128_desc(sa + TA_BYTES + 32u * kk);
+                        const uint32_t en = (it > 0 || kk > 0) ? 1u : 0u;
+                        asm volatile(
+                            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(acc),
+                            "l"(ad), "l"(bd), "r"(T_IDESC), "r"(en)
+                            : "memory");
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                     smem_u32(&empty[st]))
+                                 : "memory");
+                }
+                if (bad) break;
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&accf[buf]))
+                             : "memory");
+            }
+            if (bad) s_fail = 1;
+            // every MMA issued completes before this arrives
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_u32(&done))
+                         : "memory");
+        }
+        __syncwarp();
+    } else {
+        // epilogue: TMEM lanes 32 q .. 32 q + 31 (rows of the tile)
+        const int q = warp & 3;
+        int i = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+            const int buf = i & 1;
+            if (!g_mbar_wait(smem_u32(&accf[buf]), (uint32_t)((i >> 1) & 1))) {
+                if (lane == 0) s_fail = 1;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = base + (uint32_t)(s * T_STAGE);
-#pragma unroll
-            for (int kk = 0; kk < TK / 16; ++kk) {
-                const uint64_t ad = sw128_desc(sa + 32u * kk);
-                const uint64_t bd = sw128_desc(sa + TA_BYTES + 32u * kk);
-                const uint32_t acc = (it > 0 || kk > 0) ? 1u : 0u;
-                asm volatile(
-                    "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(ad), "l"(bd), "r"(T_IDESC), "r"(acc)
-                    : "memory");
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&empty[s]))
-                         : "memory");
-        }
-        // every MMA issued so far completes before this arrives
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&done))
-                     : "memory");
-      }
-      __syncwarp();
-    }
-    bool ok = g_mbar_wait(smem_u32(&done), 0u);
-    ok = __syncthreads_and(ok) && !s_fail;
-    if (ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int m = m0 + warp * 32 + (tid & 31);
-        float *crow = C + (int64_t)m * ldc + n0;
+            const int m = (t % tiles_m) * TM + q * 32 + lane, n0 = (t / tiles_m) * TN;
+            float *crow = C + (int64_t)m * ldc + n0;
 #pragma unroll 1
-        for (int ch = 0; ch < TN / 32; ++ch) {
-            uint32_t r[32];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * ch);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                  "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                  "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-                  "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                : "r"(taddr)
-                : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            float4 *cp = reinterpret_cast<float4 *>(crow + 32 * ch);
+            for (int ch = 0; ch < TN / 32; ++ch) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256 + 32 * ch);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr)
+                    : "memory");
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float4 *cp = reinterpret_cast<float4 *>(crow + 32 * ch);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float4 v = make_float4(alpha * __uint_as_float(r[4 * q]), alpha * __uint_as_float(r[4 * q + 1]),
-                                       alpha * __uint_as_float(r[4 * q + 2]), alpha * __uint_as_float(r[4 * q + 3]));
-                if (beta != 0.f) {
-                    const float4 o = cp[q];
-                    v.x = fmaf(beta, o.x, v.x);
-                    v.y = fmaf(beta, o.y, v.y);
-                    v.z = fmaf(beta, o.z, v.z);
-                    v.w = fmaf(beta, o.w, v.w);
+                for (int e = 0; e < 8; ++e) {
+                    float4 v = make_float4(alpha * __uint_as_float(r[4 * e]), alpha * __uint_as_float(r[4 * e + 1]),
+                                           alpha * __uint_as_float(r[4 * e + 2]),
+                                           alpha * __uint_as_float(r[4 * e + 3]));
+                    if (beta != 0.f) {
+                        const float4 o = cp[e];
+                        v.x = fmaf(beta, o.x, v.x);
+                        v.y = fmaf(beta, o.y, v.y);
+                        v.z = fmaf(beta, o.z, v.z);
+                        v.w = fmaf(beta, o.w, v.w);
+                    }
+                    cp[e] = v;
                 }
-                cp[q] = v;
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[buf])) : "memory");
         }
-    } else {
-        if (tid == 0) {
-            atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
-            // the copies still in flight land before the CTA's shared memory goes
-            for (int it = max(0, issued - TS); it < issued; ++it)
-                g_mbar_wait(smem_u32(&full[it % TS]), (uint32_t)((it / TS) & 1));
-        }
-        g_mbar_wait(smem_u32(&done), 0u);
     }
+    __syncthreads();
+    if (s_fail && tid == 0) {
+        atomicCAS(&ctl->status, 0, (int)GBP_ERR_TIMEOUT);
+        // the copies still in flight land before the CTA's shared memory goes
+        for (int g = max(0, issued - TS); g < issued; ++g)
+            g_mbar_wait(smem_u32(&full[g % TS]), (uint32_t)((g / TS) & 1));
+    }
+    if (tid == 32) g_mbar_wait(smem_u32(&done), 0u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(T_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TP_TMEM_COLS)
                      : "memory");
     }
 }
@@ -596,7 +638,9 @@ gbp_status gbp_nn_gemm_bf16(gbp_ctx *c, int32_t M, int32_t N, int32_t Kp, const 
         ((uintptr_t)B & 15) == 0 && ((uintptr_t)C & 15) == 0 && make_tile_map(&ta, A, M, Kp, lda, TM) &&
         make_tile_map(&tb, B, N, Kp, ldb, TN)) {
         cudaFuncSetAttribute(k_gemm_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, T_SMEM);
-        k_gemm_tma<<<dim3(M / TM, N / TN), 128, T_SMEM, c->stream>>>(Kp, ta, tb, C, ldc, alpha, beta, c->ctl);
+        const int ntiles = (M / TM) * (N / TN);
+        k_gemm_tma<<<min(ntiles, c->num_sms), 192, T_SMEM, c->stream>>>(M, N, Kp, ta, tb, C, ldc, alpha, beta,
+                                                                         c->ctl);
         c->launches++;
         return st_of(cudaGetLastError());
     }

@@ -3,7 +3,8 @@ kernels) against the FP64 reference network (oracle/nn_oracle.py).
 
 Tolerances: the GEMM (both kernels: the 128 x 64 tile kernel and, for
 shapes of at least 64 whole 128 x 256 tiles, the TMA-fed one) against an FP64 product of
-the same BF16-rounded operands (FP32 accumulation: 1e-5 relative); the whole network (every GEMM
+the same BF16-rounded operands (FP32 accumulation: 1e-5 relative; at 8192^3-class
+sizes against a PyTorch FP32 product of the same operands); the whole network (every GEMM
 operand rounded to BF16, 2^-9 relative each, through six layers) against the
 FP64 reference with FP32 weights: 3e-2 relative L2 for outputs and
 gradients."""
@@ -39,9 +40,10 @@ def bf16_round(x):
     return r.astype(np.uint32).view(np.float32)
 
 
-# the last two are 64 and 72 whole 128 x 256 tiles: the TMA-fed kernel
+# the last three are 64, 72 and 320 whole 128 x 256 tiles: the TMA-fed kernel
+# (at 320 tiles some CTAs take three, so each of its two accumulators is reused)
 @pytest.mark.parametrize("M,N,K", [(300, 100, 130), (128, 64, 64), (1, 43, 256), (1000, 320, 1216),
-                                   (1024, 2048, 320), (1152, 2048, 1216)])
+                                   (1024, 2048, 320), (1152, 2048, 1216), (4096, 2560, 128)])
 def test_gemm_bf16(ctx, M, N, K):
     rng = np.random.default_rng(M + N + K)
     Kp = ((K + 63) // 64) * 64
@@ -60,6 +62,30 @@ def test_gemm_bf16(ctx, M, N, K):
     ref = 0.5 * (A.astype(np.float64) @ B.astype(np.float64).T) + 2.0 * C0
     assert ctx.stats()["status"] == 0
     assert rel_l2(Cd.cpu().numpy(), ref) < 1e-5
+
+
+def test_gemm_bf16_large_vs_fp32_matmul(ctx):
+    """The TMA-fed kernel at the size its throughput is reported at (8192 x
+    8192 x 4096: 2048 tiles, 13-14 per CTA) against a plain PyTorch FP32
+    product of the same BF16 operands (no TF32): 1e-5 relative L2."""
+    M = N = 8192
+    K = 4096
+    g = torch.Generator(device="cuda").manual_seed(7)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    C0 = torch.randn(M, N, device="cuda", generator=g)
+    Cd = C0.clone()
+    st = ctx.lib.gbp_nn_gemm_bf16(ctx.h, M, N, K, C.c_void_p(A.data_ptr()), K, C.c_void_p(B.data_ptr()), K,
+                                  C.c_void_p(Cd.data_ptr()), N, 0.5, 2.0)
+    assert st == 0 and ctx.stats()["status"] == 0
+    tf32 = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        ref = 0.5 * (A.float() @ B.float().T) + 2.0 * C0
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+    err = float(torch.linalg.vector_norm(Cd - ref) / torch.linalg.vector_norm(ref))
+    assert err < 1e-5, err
 
 
 def test_network_forward_backward_vs_reference(ctx):
