@@ -311,7 +311,7 @@ def main():
             return ctx.forward_backward_batch_host(hin[0], hin[1], hin[3], p.tmpl, t=hin[2], opts=opts,
                                                    precision=prec, out=hout)
 
-        for _ in range(2):
+        for _ in range(max(3, args.warmup)):
             e2e_step()
         if dist is not None:
             dist.barrier()
@@ -324,7 +324,7 @@ def main():
                "d2h_bytes_per_step": int(sum(h.nbytes for h in hout.values()))}
     if not args.no_e2e and B == 1:
         h_out = None
-        for _ in range(2):
+        for _ in range(max(3, args.warmup)):
             h_out = ctx.forward_backward_host(cf_np, ct_np, target_np, p.tmpl, t=ons.t, opts=opts,
                                               precision=prec, out=h_out)
         if dist is not None:
