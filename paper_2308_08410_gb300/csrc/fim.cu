@@ -80,7 +80,9 @@ constexpr int FIM_MINB = GBP_FIM_MINB;
 // record of the next round (read before this round's solve).  Measured on 16
 // problems of the 72^3 cube: 22.12 -> 21.65 ms (the record alone: 21.74 ms;
 // also the next vertex's adjacency range: 21.88 ms; also the next round's
-// velocity terms or face values: 22.9 / 22.5 ms).
+// velocity terms or face values: 22.9 / 22.5 ms).  L1 / L2 prefetch
+// instructions for the fibre, the positions or the next velocity terms cost
+// more issue slots than they saved (21.9 / 21.7 ms against 21.5).
 // Register budget (64 at 32 warps per SM): only what the face loop needs is
 // held across it; the vertex's own position is re-read per face (an L1
 // hit), its own value and change stamp and its neighbour range after the
@@ -174,6 +176,17 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int g, bool 
             }
         }
     }
+    // the vertex's own value and change stamp and its neighbour range, issued
+    // before the reduction so that their latency overlaps it (only this group
+    // writes the vertex in this iteration, so the value read now is the one
+    // the iteration began with)
+    int2 own = make_int2(0, 0);
+    int nb0 = 0, ne0 = 0;
+    if (act) {
+        own = FIM_LD(&a.pc[gi]);
+        nb0 = __ldg(&a.n2n_ptr[gi - boff]);
+        ne0 = __ldg(&a.n2n_ptr[gi - boff + 1]);
+    }
     // lexicographic (value, code) minimum over the group
 #pragma unroll
     for (int off = G / 2; off > 0; off >>= 1) {
@@ -184,12 +197,9 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int g, bool 
             best_code = oc;
         }
     }
-    // the vertex's own value and change stamp: only this group writes them in
-    // this iteration, so the value read now is the one the iteration began with
     bool changed = false;
     int nb = 0, ne = 0;
     if (act) {
-        const int2 own = FIM_LD(&a.pc[gi]);
         const float phi_old = __int_as_float(own.x);
         if (best < phi_old) {
             changed = (phi_old == GBP_INF) || (phi_old - best > a.eps);
@@ -200,8 +210,8 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int g, bool 
             }
         }
         if (changed) {
-            nb = __ldg(&a.n2n_ptr[gi - boff]);
-            ne = __ldg(&a.n2n_ptr[gi - boff + 1]);
+            nb = nb0;
+            ne = ne0;
         }
     }
     // activate the neighbours of changed vertices for iteration k+1
