@@ -214,14 +214,20 @@ __device__ __forceinline__ void fim_vertex(const FimArgs &a, int k, int g, bool 
             ne = ne0;
         }
     }
-    // activate the neighbours of changed vertices for iteration k+1
+    // activate the neighbours of changed vertices for iteration k+1: two per
+    // lane and pass (a Kuhn vertex has 14 neighbours: one pass of an 8-lane
+    // group), so that the two stamps' atomics overlap (16 problems: 21.34 ->
+    // 20.80 ms against one neighbour per lane and pass)
     const int maxn = __reduce_max_sync(0xffffffffu, ne - nb);
-    for (int e0 = 0; e0 < maxn; e0 += G) {
-        const int e = nb + e0 + sub;
-        if (e < ne) {
-            const int m = boff + __ldg(&a.n2n[e]);
-            if (atomicMax(&a.stamp[m], k + 1) < k + 1) nlist[atomicAdd(&a.ctl->count[nxt], 1)] = m;
-        }
+    for (int e0 = 0; e0 < maxn; e0 += 2 * G) {
+        const int ea = nb + e0 + sub, eb = ea + G;
+        const bool va = ea < ne, vb = eb < ne;
+        const int ma = va ? boff + __ldg(&a.n2n[ea]) : 0;
+        const int mb = vb ? boff + __ldg(&a.n2n[eb]) : 0;
+        const int sa = va ? atomicMax(&a.stamp[ma], k + 1) : k + 1;
+        const int sb = vb ? atomicMax(&a.stamp[mb], k + 1) : k + 1;
+        if (sa < k + 1) nlist[atomicAdd(&a.ctl->count[nxt], 1)] = ma;
+        if (sb < k + 1) nlist[atomicAdd(&a.ctl->count[nxt], 1)] = mb;
     }
 }
 
