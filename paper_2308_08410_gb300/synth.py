@@ -6,7 +6,8 @@ no eikonal iteration, no ECG contraction, no gradient).  It only produces the
 *inputs* the paper's method consumes:
 
 * P1 simplicial meshes (Sec. II-A: "simplicial triangulation", one metric per
-  element): Kuhn-split cubes and voxel-Kuhn biventricular shells;
+  element): Kuhn-split cubes, voxel-Kuhn biventricular shells and
+  Delaunay tetrahedralisations of random points;
 * fibre directions and the two conduction velocities per element (the
   orthotropic conduction tensor of Eq. (1) is built from them by each side on
   its own);
@@ -34,12 +35,12 @@ import numpy as np
 __all__ = [
     "Mesh", "Onsets", "Template", "Problem", "TriMesh", "Problem2D", "make_2d",
     "lv_slice", "lead_field_2d", "locate_2d", "make_2d_torso",
-    "kuhn_cube", "voxel_kuhn", "biv_shell_mask",
+    "kuhn_cube", "voxel_kuhn", "biv_shell_mask", "delaunay_cloud",
     "fibres_cube", "fibres_biv", "smooth_field", "nodal_to_tet_mean",
     "fibonacci_sphere", "torso_electrodes", "lead_field", "twelve_lead_matrix",
     "onsets_nodal", "onsets_element", "onsets_surface",
     "add_noise", "boundary_faces",
-    "make_c1", "make_c2", "make_c3", "make_c4_phi", "make_c4",
+    "make_c1", "make_c2", "make_c3", "make_c4_phi", "make_c4", "make_delaunay",
     "c5_sample_params", "random_faces",
 ]
 
@@ -162,6 +163,27 @@ def kuhn_slab(n: int, layers: int, hz: float, side: float = 10.0) -> Mesh:
     xyz = xyz[keep_v]
     xyz[:, 2] *= hz / h
     return Mesh(xyz.astype(np.float32), tets)
+
+
+def delaunay_cloud(n_pts: int, seed: int, side: float = 10.0, sliver: float = 0.02) -> Mesh:
+    """Unstructured mesh: the Delaunay tetrahedralisation (scipy) of n_pts
+    uniform random points in [0, side]^3, each tet oriented positively, tets
+    below `sliver` x the mean volume dropped, unused points removed.  About
+    26 incident tets and 15 neighbours per vertex on average, up to ~80 and
+    ~45 at 20,000 points (a Kuhn lattice: at most 24 and 14)."""
+    from scipy.spatial import Delaunay
+    r = np.random.default_rng(seed)
+    pts = r.uniform(0.0, side, (n_pts, 3))
+    t = Delaunay(pts).simplices.astype(np.int64)
+    det = np.linalg.det(pts[t[:, 1:]] - pts[t[:, :1]])
+    neg = det < 0
+    t[neg] = t[neg][:, [0, 2, 1, 3]]
+    vol = np.abs(det) / 6.0
+    t = t[vol > sliver * vol.mean()]
+    used = np.unique(t)
+    remap = np.full(n_pts, -1, np.int64)
+    remap[used] = np.arange(used.size)
+    return Mesh(pts[used].astype(np.float32), remap[t].astype(np.int32))
 
 
 def voxel_kuhn(mask: np.ndarray, h: float, origin) -> Mesh:
@@ -451,6 +473,22 @@ def make_c1(n: int = 20, seed: int = 0, side: float = 10.0, n_leads: int = 8,
     el = fibonacci_sphere(n_leads, 30.0, (side / 2,) * 3)
     L = lead_field(mesh, el)
     return Problem("c1", mesh, fib, cf, ct, ons, L, Template(-80.0, 20.0, 1.0, 0.0, 1.0, T))
+
+
+def make_delaunay(n_pts: int = 1500, seed: int = 0, side: float = 10.0, n_leads: int = 8,
+                  T: int = 150) -> Problem:
+    """The c1 set-up on an unstructured mesh (delaunay_cloud): fibres rotating
+    with depth, c_f = 0.6 / c_t = 0.3 mm/ms with 5 % per-tet jitter, 3
+    element onsets t ~ U[0, 6] ms, 8 electrodes on a 30 mm sphere."""
+    mesh = delaunay_cloud(n_pts, seed, side)
+    fib = fibres_cube(mesh, side)
+    r = np.random.default_rng(seed + 1234)
+    cf = (0.6 * (1 + 0.05 * r.standard_normal(mesh.n_t))).astype(np.float32)
+    ct = (0.3 * (1 + 0.05 * r.standard_normal(mesh.n_t))).astype(np.float32)
+    ons = onsets_element(mesh, 3, seed=seed + 7, tmin=0.0, tmax=6.0)
+    el = fibonacci_sphere(n_leads, 30.0, (side / 2,) * 3)
+    L = lead_field(mesh, el)
+    return Problem("delaunay", mesh, fib, cf, ct, ons, L, Template(-80.0, 20.0, 1.0, 0.0, 1.0, T))
 
 
 def make_c2(h: float = 1.0, seed: int = 0, T: int = 300, fast_layer_mm: float = 1.0) -> Problem:

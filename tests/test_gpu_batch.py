@@ -35,8 +35,10 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def batch_problem(n, B, seed, kind="element"):
-    p = S.make_c1(n=n, seed=seed)
+def batch_problem(n, B, seed, kind="element", base=None):
+    """B velocity fields and onset times around a base problem (the c1 cube
+    of n^3 vertices unless `base` is given) and their targets."""
+    p = S.make_c1(n=n, seed=seed) if base is None else base
     if kind == "element":
         p.onsets = S.onsets_element(p.mesh, 3, seed=seed + 7, tmin=0.0, tmax=6.0)
     r = np.random.default_rng(seed + 99)
@@ -100,6 +102,21 @@ def test_batch_matches_oracle_and_single(ctx, kind):
         for k in keys:
             assert rel_l2(g[k][b], one[k].cpu().numpy()) < 1e-4, (b, k)
         gbp.setup_problem(ctx, p)
+
+
+def test_batch_on_an_unstructured_mesh(ctx):
+    """Three problems on a Delaunay mesh (8,000 random points: up to 72
+    incident tets and 40 neighbours per vertex), each against the oracle."""
+    B = 3
+    p, cf, ct, t, tg = batch_problem(0, B, seed=3, base=S.make_delaunay(n_pts=8000, seed=3))
+    gbp.setup_problem(ctx, p)
+    out = ctx.forward_backward_batch(dev(cf), dev(ct), dev(tg), p.tmpl, t=dev(t))
+    st = ctx.stats()
+    assert st["status"] == 0, st
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    for b in range(B):
+        ons = S.Onsets(p.onsets.kind, p.onsets.idx, t[b], p.onsets.bary)
+        check_problem(ctx, g, b, p, cf[b], ct[b], ons, tg[b], ("d_cf", "d_ct", "d_t", "d_x"))
 
 
 def test_batch_of_one_and_state(ctx):

@@ -174,6 +174,19 @@ def test_eikonal_biv(ctx, jitter):
     assert PH.unambiguous(ref).mean() > (0.99 if jitter else 0.9)
 
 
+def test_eikonal_delaunay(ctx):
+    """An unstructured Delaunay mesh (20,000 random points, 133k tets): its
+    vertices have up to 76 incident tets (ten face rounds of an 8-lane
+    group, against three on a Kuhn lattice) and up to 44 neighbours (three
+    activation passes, against one); phi, every unambiguous parent and alpha
+    against the oracle."""
+    p = S.make_delaunay(n_pts=20000, seed=1)
+    inc = np.bincount(p.mesh.tets.ravel(), minlength=p.mesh.n_v)
+    assert inc.max() > 40
+    g, par, al, ref, st = check_eikonal(ctx, p)
+    assert PH.unambiguous(ref).mean() > 0.98
+
+
 def test_eikonal_eps_and_unreached(ctx):
     a = S.kuhn_cube(6, 1.0)
     xyz = np.concatenate([a.xyz, a.xyz + np.float32(3.0)])

@@ -16,6 +16,8 @@ OK, INVALID, BAD = 0, 1, 2
 def test_valid_meshes_pass():
     m = S.kuhn_cube(5, 10.0)
     assert gbp.check_mesh(m.xyz, m.tets) == OK
+    m = S.delaunay_cloud(800, 5)
+    assert gbp.check_mesh(m.xyz, m.tets) == OK
     t = S.tri_square(9, 10.0, jitter=0.3, seed=2)
     assert gbp.check_mesh_2d(t.xy, t.tris) == OK
     xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], np.float32)
@@ -133,9 +135,12 @@ def test_adjacency_matches_its_definition():
     """The vertex->tet lists (ascending tet * 4 + slot), the neighbour lists
     (sorted, unique) and the FIM's face records (the other three vertices in
     slot order) equal a brute-force construction: on a Kuhn cube, on random
-    tets over a few vertex ids (shared faces, isolated vertices) and on a
-    single tet."""
+    tets over a few vertex ids (shared faces, isolated vertices), on a
+    single tet; and on an unstructured Delaunay mesh, whose vertices have up
+    to 40 incident tets."""
     m = S.kuhn_cube(4, 10.0)
+    check_adjacency(m.tets, m.n_v)
+    m = S.delaunay_cloud(300, 6)
     check_adjacency(m.tets, m.n_v)
     r = np.random.default_rng(3)
     for _ in range(10):
