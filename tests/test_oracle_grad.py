@@ -31,6 +31,17 @@ def small_problem(n=10, kind="element", seed=0, K=3):
     return p
 
 
+def delaunay_small_problem(n_pts=800, seed=1):
+    """synth.make_delaunay (jittered velocities, element onsets) with a target
+    built as in small_problem."""
+    p = S.make_delaunay(n_pts=n_pts, seed=seed)
+    rng = np.random.default_rng(seed + 99)
+    cf2 = (p.cf * (1 + 0.1 * rng.standard_normal(p.mesh.n_t))).astype(np.float32)
+    ek = O.eikonal(p.mesh, p.fib, cf2, p.ct, p.onsets)
+    p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, seed + 5)
+    return p
+
+
 def evaluate(p):
     return O.forward_backward(p.mesh, p.fib, p.cf, p.ct, p.onsets, p.L, p.tmpl, p.extra["target"])
 
@@ -44,25 +55,33 @@ def parent_matrix(mesh, parent, alpha):
     return sp.coo_matrix((alpha[idx].ravel(), (np.repeat(idx, 3), fv.ravel())), shape=(n, n)).tocsc()
 
 
-def test_adjoint_matches_sparse_solve():
-    """mu = (I - P^T)^{-1} lam with SuperLU, on the BiV-shaped mesh whose
-    parent graph holds cycles (the oracle's SCC ordering must agree)."""
-    p = S.make_c2(h=1.6)
+@pytest.mark.parametrize("mesh", ["biv", "delaunay"])
+def test_adjoint_matches_sparse_solve(mesh):
+    """mu = (I - P^T)^{-1} lam with SuperLU, on meshes whose parent graph
+    holds cycles (the oracle's SCC ordering must agree): the BiV-shaped mesh,
+    and a 3,000-point Delaunay mesh with cycles of up to 15 vertices."""
+    p = S.make_c2(h=1.6) if mesh == "biv" else S.make_delaunay(n_pts=3000, seed=2)
     ek = O.eikonal(p.mesh, p.fib, p.cf, p.ct, p.onsets)
     rng = np.random.default_rng(0)
     lam = rng.normal(size=p.mesh.n_v)
     g = O.adjoint(p.mesh, p.fib, p.cf, p.ct, p.onsets, ek["parent"], ek["alpha"], lam)
     P = parent_matrix(p.mesh, ek["parent"], ek["alpha"])
+    if mesh == "delaunay":
+        from scipy.sparse.csgraph import connected_components
+        _, lab = connected_components((P != 0).astype(float), directed=True, connection="strong")
+        assert np.bincount(lab).max() > 2
     mu = spl.spsolve((sp.eye(p.mesh.n_v) - P.T).tocsc(), lam)
     assert g["unprocessed"] == 0
     np.testing.assert_allclose(g["mu"], mu, rtol=1e-9, atol=1e-12 * np.abs(mu).max())
 
 
-def test_fd_fifty_parameters():
+@pytest.mark.parametrize("mesh", ["kuhn", "delaunay"])
+def test_fd_fifty_parameters(mesh):
     """Central differences (h = 1e-4) on 50 random parameters (per-tet c_f,
-    c_t, onset times).  A probe whose +-h solves change a parent with margin
+    c_t, onset times), on the jittered Kuhn cube and on an unstructured
+    Delaunay mesh.  A probe whose +-h solves change a parent with margin
     below 1e-5 sits on a kink of the piecewise-smooth loss and is redrawn."""
-    p = small_problem(n=9)
+    p = small_problem(n=9) if mesh == "kuhn" else delaunay_small_problem()
     r = evaluate(p)
     rng = np.random.default_rng(4)
     g = {"cf": r["d_cf"], "ct": r["d_ct"], "t": r["d_t"]}
