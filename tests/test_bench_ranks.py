@@ -1,7 +1,8 @@
 """Host logic of the benchmark on CPU: one replica per rank, the
 job's time is the slowest rank's (all_reduce MAX over two gloo ranks), the
 value is every rank's units over that time, and under torchrun only rank 0
-runs the oracle arm while the other ranks leave without work; the stored
+runs the oracle arm while the other ranks leave without work, and that arm
+prints the contract's line; the stored
 ncu traffic figure is reported only for the kernel it was captured on."""
 import json
 import os
@@ -74,6 +75,28 @@ def test_reference_arm_on_other_ranks_does_nothing(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "0")
     bench.main()
     assert len(called) == 1 and called[0][1] == 2     # rank 0 runs it, with the world size
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """The oracle arm on a 10^3 cube (two steps): one JSON line with the
+    metric of the benchmarked workload, its own cpu_baseline and an e2e that
+    moves no bytes, in FP64 on the host cores."""
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3",
+                                      "--n", "10"])
+    bench.main()
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRICS["c3"]
+    assert d["unit"] == "evals/s" and d["higher_is_better"] is True and d["dtype"] == "f64"
+    assert d["n_gpus"] == 1 and d["steps"] == 2 and d["value"] > 0
+    assert abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    assert d["config"]["n"] == 10 and d["config"]["n_v"] == 1000
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
 def test_stored_traffic_applies_only_to_its_kernel(tmp_path):
