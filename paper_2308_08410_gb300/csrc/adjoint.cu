@@ -27,9 +27,11 @@
 // readies go to a work queue of (vertex, mu) pairs.  The critical path is
 // the depth of the parent graph times one vertex's latency.  The parent
 // graph of the discrete fixed point can hold short cycles (non-causal
-// updates in anisotropic elements); the vertices they block are finished by
-// a bounded fixed-point (Jacobi) iteration on the remaining sub-graph, which
-// is closed under taking parents.  Most of those cycles are 2-cycles (c's
+// updates in anisotropic elements); the vertices they block (the longer
+// cycles and all their ancestors) are finished by a bounded fixed-point
+// (Jacobi) iteration on that sub-graph, which is closed under taking
+// parents, in the words' fixed point and stopped per vertex (below).  Most of
+// those cycles are 2-cycles (c's
 // parent face holds p and p's holds c); they are solved exactly inside the
 // dataflow instead: the edge between the two is left out of their counts,
 // and once both have every other child, the second of the two to be ready
@@ -71,7 +73,8 @@ struct AdjArgs {
     const int *on_idx;
     const float *on_bary;
     const float *lam;
-    float *mu, *xj, *acc, *acc2;
+    float *mu;
+    unsigned long long *xj, *acc, *acc2;  // cycle iteration: x and the pushes, in the words' fixed point
     unsigned long long *w;  // packed (child count, fixed-point lambda + push sum) per vertex
     unsigned int *done;     // processed vertex entries (bitmap)
     int *lists;
@@ -586,12 +589,11 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
         const int64_t i = base + tid;
         bool app = i < n_tot && !is_done(a.done, i);
         if (app) {
-            // base value: lambda plus the pushes of the processed children
-            const float b0 = (float)((double)adj_sum(__ldcg(&a.w[i])) * iscale);
-            a.mu[i] = b0;
-            a.xj[i] = b0;
-            a.acc[i] = 0.f;
-            a.acc2[i] = 0.f;
+            // x starts from the base (lambda plus the pushes of the processed
+            // children, the sum in the vertex's word); the base stays there
+            a.xj[i] = (unsigned long long)adj_sum(__ldcg(&a.w[i]));
+            a.acc[i] = 0ull;
+            a.acc2[i] = 0ull;
         }
         warp_append(app, (int)i, R, &a.ctl->count[3]);
     }
@@ -599,61 +601,55 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     if (!grid_barrier(a.ctl, a.grp, nbar)) return;
     const int nR = ld_relaxed_i32(&a.ctl->count[3]);
     if (nR == 0) return;
-    // x <- base + P_R^T x with base = mu (lam plus the pushes of processed
-    // children).  One barrier per iteration: the update of x reads the sums
+    // x <- base + P_R^T x in the words' fixed point (integer sums: the result
+    // does not depend on the order of the pushes, and a settled vertex stops
+    // changing).  One barrier per iteration: the update of x reads the sums
     // pushed in the previous iteration (buffer cur) and pushes the new x into
-    // the other buffer.  Stop when max |dx| <= 2e-6 max |x| over all of R
-    // (FP32 sums in varying atomic order jitter by about an ulp).
-    float *acc_cur = a.acc, *acc_nxt = a.acc2;
-    auto push = [&](int i, float x, float *dst) {
+    // the other buffer.  Stop when every vertex of R changed by at most
+    // |x| 2^-23 + 8192 units (about 1e-7 relative, plus 2^-40 sum |lambda|).
+    // A stop against the largest |x| of R instead left vertices with small mu,
+    // and ancestors still receiving pushes, far from their fixed point.
+    unsigned long long *acc_cur = a.acc, *acc_nxt = a.acc2;
+    auto push = [&](int i, long long x, unsigned long long *dst) {
         const ARec r = load_arec(a.arec, i);
         if (r.jt < 0) return;
         const int boff = (i / (int)n_v) * (int)n_v;
 #pragma unroll
         for (int q = 0; q < 3; ++q)
-            if (r.f[q] >= 0) atomicAdd(&dst[boff + r.f[q]], r.a[q] * x);
+            if (r.f[q] >= 0)
+                atomicAdd(&dst[boff + r.f[q]], (unsigned long long)__double2ll_rn((double)r.a[q] * (double)x));
     };
     for (int64_t w = tid; w < nR; w += nth) {
         const int i = __ldcg(&R[w]);
-        push(i, ld_cg_f(&a.xj[i]), acc_cur);
+        push(i, (long long)__ldcg(&a.xj[i]), acc_cur);
     }
     ++nbar;
     if (!grid_barrier(a.ctl, a.grp, nbar)) return;
     int it = 0;
     for (; it < a.max_cycle_iters; ++it) {
         // slot (it+1)%3 was last read before the previous barrier
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            a.ctl->adj_delta[(it + 1) % 3] = 0.f;
-            a.ctl->adj_xmax[(it + 1) % 3] = 0.f;
-        }
-        float dmax = 0.f, xmax = 0.f;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->adj_delta[(it + 1) % 3] = 0.f;
+        int viol = 0;
         for (int64_t w = tid; w < nR; w += nth) {
             const int i = __ldcg(&R[w]);
-            const float xn = ld_cg_f(&a.mu[i]) + ld_cg_f(&acc_cur[i]);
-            const float xo = ld_cg_f(&a.xj[i]);
-            acc_cur[i] = 0.f;
-            dmax = fmaxf(dmax, fabsf(xn - xo));
-            xmax = fmaxf(xmax, fabsf(xn));
-            a.xj[i] = xn;
+            const long long xn = adj_sum(__ldcg(&a.w[i])) + (long long)__ldcg(&acc_cur[i]);
+            const long long xo = (long long)__ldcg(&a.xj[i]);
+            acc_cur[i] = 0ull;
+            const long long d = xn > xo ? xn - xo : xo - xn;
+            const long long ax = xn < 0 ? -xn : xn;
+            viol += d > (ax >> 23) + 8192;
+            a.xj[i] = (unsigned long long)xn;
             push(i, xn, acc_nxt);
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
-            xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, off));
-        }
-        if ((threadIdx.x & 31) == 0) {
-            if (dmax > 0.f) atomicMax((int *)&a.ctl->adj_delta[it % 3], __float_as_int(dmax));
-            if (xmax > 0.f) atomicMax((int *)&a.ctl->adj_xmax[it % 3], __float_as_int(xmax));
-        }
+        viol = __reduce_add_sync(0xffffffffu, viol);
+        if ((threadIdx.x & 31) == 0 && viol) atomicAdd((int *)&a.ctl->adj_delta[it % 3], viol);
         ++nbar;
         if (!grid_barrier(a.ctl, a.grp, nbar)) return;
-        const float gd = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_delta[it % 3]));
-        const float gx = __int_as_float(ld_relaxed_i32((const int *)&a.ctl->adj_xmax[it % 3]));
-        float *t = acc_cur;
+        const int gv = ld_relaxed_i32((const int *)&a.ctl->adj_delta[it % 3]);
+        unsigned long long *t = acc_cur;
         acc_cur = acc_nxt;
         acc_nxt = t;
-        if (gd <= 2e-6f * gx) {
+        if (gv == 0) {
             ++it;
             break;
         }
@@ -666,7 +662,7 @@ __global__ void __launch_bounds__(256) k_adjoint(AdjArgs a)
     }
     for (int64_t w = tid; w < nR; w += nth) {
         const int i = __ldcg(&R[w]);
-        const float x = ld_cg_f(&a.xj[i]);
+        const float x = (float)((double)(long long)__ldcg(&a.xj[i]) * iscale);
         a.mu[i] = x;
         atomicOr(&a.done[i >> 5], 1u << (i & 31));
         const int b = i / (int)n_v;

@@ -43,8 +43,8 @@ struct Control {
     int adj_cycle_nodes;
     int adj_cycle_iters;
     int adj_processed;
-    float adj_delta[3];           // max |dx| of the cycle iteration (rotating slots)
-    float adj_xmax[3];            // max |x| of the cycle iteration (rotating slots)
+    float adj_delta[3];           // cycle iteration: vertices not yet settled, as int bits (rotating slots)
+    float adj_xmax[3];            // spare
     double adj_lsum;              // sum |dL/dphi| (scale of the adjoint's fixed-point sums)
     unsigned long long adj_ts[3]; // global timer at adjoint start, end of dataflow, end
     int n_defer;                  // FIM faces deferred to the FP64 repair (entries written, may exceed the cap)

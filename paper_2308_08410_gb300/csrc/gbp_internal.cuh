@@ -70,7 +70,8 @@ struct gbp_ctx {
     int2 *defer = nullptr;  // FIM faces deferred to the FP64 repair: (vertex entry, face record index)
     int rec_nb = 0;  // problems held in the solution (phi, parent record) of the last solve (0: none)
     // adjoint state
-    float *mu = nullptr, *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;
+    float *mu = nullptr;
+    unsigned long long *jac_x = nullptr, *jac_acc = nullptr, *jac_acc2 = nullptr;  // cycle iteration, fixed point
     unsigned long long *adj_w = nullptr;  // adjoint: packed (child count, push sum) per vertex
     int *adj_cand = nullptr, *adj_pair = nullptr;  // adjoint: 2-cycle candidates and partners per vertex
     unsigned long long *adj_pairw = nullptr;       // adjoint: hand-over word of each 2-cycle (at its smaller entry)

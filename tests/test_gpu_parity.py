@@ -187,6 +187,22 @@ def test_eikonal_delaunay(ctx):
     assert PH.unambiguous(ref).mean() > 0.98
 
 
+def test_gradient_delaunay(ctx):
+    """Loss, gradients and per-tet velocity gradients on the 20,000-point
+    Delaunay mesh (seed 2).  Its parent graph holds cycles longer than two;
+    they and all their ancestors (about half the vertices) are finished by
+    the adjoint's fixed-point iteration, which has to settle every vertex,
+    not only those with the largest mu, for the per-tet gradients to hold."""
+    p = S.make_delaunay(n_pts=20000, seed=2)
+    ek = O.eikonal(p.mesh, p.fib, (p.cf * 1.07).astype(np.float32), p.ct, p.onsets)
+    p.extra["target"] = S.add_noise(O.ecg(p.L, ek["phi"], p.tmpl), 0.05, 7)
+    g, ref, st = gradient_case(ctx, p)
+    assert st["adj_cycle_nodes"] > 1000
+    assert abs(g["loss"][0] - ref["loss"]) / ref["loss"] < 1e-4
+    for k in ("d_cf", "d_ct", "d_t", "d_x"):
+        assert rel_l2(g[k], ref[k]) < 1e-3, (k, rel_l2(g[k], ref[k]), st)
+
+
 def test_eikonal_eps_and_unreached(ctx):
     a = S.kuhn_cube(6, 1.0)
     xyz = np.concatenate([a.xyz, a.xyz + np.float32(3.0)])
